@@ -1,0 +1,413 @@
+#!/usr/bin/env python
+"""Throughput of the NeRF-CBCT training step on GB300 (ray-samples/s, fwd+bwd+Adam).
+
+A step is one pass of the whole hot path over one batch: ray setup and sampling,
+hash gather, Normalized Hash Encoder, MLP, Beer-Lambert ray sum, loss, the
+backward (MLP, LN, hash scatter) and Adam over every parameter. The default
+workload is the paper-scale FP32 configuration: a 128^3 textured ellipsoid
+phantom, 50 views of a 256x256 detector, L=16 F=2 T=2^19 levels 16..2048,
+LayerNorm, 4x32 MLP, 2048 rays x 192 samples per step. Inputs are synthetic
+(seeded phantom projected by the library, Poisson noise at I0 = 1e5); every
+batch uses pixels whose ray meets the volume.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun), every rank trains its own replica on its own batches
+(weak scaling, no collective on the data path); value = all ranks' samples / the
+slowest rank's time. ``--impl reference`` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import signal
+import subprocess
+import sys
+import tempfile
+import time
+
+if "--cpu-worker" in sys.argv or "reference" in sys.argv:
+    for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[_v] = "1"          # the CPU oracle runs on one core
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic as S  # noqa: E402
+
+METRIC = "ray-samples/s fwd+bwd; seconds to 30 dB PSNR, mixed vs FP32, same GB300"
+UNIT = "ray-samples/s"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="paper_fp32", choices=sorted(S.WORKLOADS))
+    p.add_argument("--mixed", default="paper_bf16", help="mixed-precision workload measured beside ('' = skip)")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--seed", type=int, default=0)
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------------------ CPU oracle
+def oracle_sample_rays(w: S.Workload, seconds: float, seed: int):
+    """Oracle train steps on bounded batches (same field shape, N and geometry)
+    until about ``seconds`` of work; returns (samples, seconds, description)."""
+    import oracle
+    g, f = w.geometry, w.field
+    tab, du, dv = oracle.view_table(g.n_views, g.angle0_rad, g.span_rad, g.dso_mm, g.dsd_mm,
+                                    g.det_du_mm, g.det_dv_mm, g.vol_side_mm)
+    og = (tab, du, dv, g.det_nu, g.det_nv)
+    rng = np.random.default_rng(seed)
+    flat = S.init_params(f, seed).astype(np.float64)
+    st = oracle.AdamState.zeros(flat.size)
+    R = 16
+    samples, t0, steps = 0, time.perf_counter(), 0
+    while True:
+        view = int(rng.integers(0, g.n_views))
+        _, _, _, _, hit = oracle.ray_setup(tab, du, dv, g.det_nu, g.det_nv, view,
+                                           np.arange(g.det_nu * g.det_nv))
+        pix = rng.choice(np.nonzero(hit)[0], size=R, replace=False).astype(np.int32)
+        a_meas = rng.uniform(0, 1, size=R).astype(np.float32)
+        flat, st, _, _ = oracle.train_step(flat, st, f, og, view, pix, a_meas, w.n_samples)
+        samples += R * w.n_samples
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    desc = (f"{steps} oracle train steps of {R} rays x {w.n_samples} samples on the {w.name} field "
+            f"(T=2^{f.log2_T}, L={f.n_levels}, dense Adam over all {flat.size} parameters), float64 numpy")
+    return samples, el, desc
+
+
+def cpu_baseline(w: S.Workload, seconds: float, seed: int):
+    """Runs the oracle in a fresh single-threaded interpreter (BLAS pinned to 1 thread)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", "--workload", w.name,
+           "--cpu-seconds", str(seconds), "--seed", str(seed)]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=seconds * 10 + 120)
+    if r.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": r.stderr[-300:]}
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": out["value"], "unit": UNIT, "cores": 1, "kind": "oracle", "sample": out["sample"]}
+
+
+# ------------------------------------------------------------------------------ GPU helpers
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return FALLBACK_PEAKS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.index)], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.send_signal(signal.SIGTERM)
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2506_19742_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current sources."""
+    p = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    m1 = re.search(r"source_sha:\s*([0-9a-f]+)", txt)
+    m2 = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not m1 or not m2 or m1.group(1) != source_sha():
+        return None
+    return float(m2.group(1))
+
+
+def make_scan(nh, torch, w: S.Workload, seed: int, device):
+    """Phantom, measured projections (library projector + Poisson noise) and the
+    per-view pixels whose rays meet the volume."""
+    geom = nh.Geometry.from_config(w.geometry)
+    vol, _ = S.phantom(w, seed)
+    D = vol.shape[0]
+    g = w.geometry
+    proj = torch.empty(g.n_views * g.det_nv * g.det_nu, device=device)
+    nh.project(geom, torch.from_numpy(vol.astype(np.float32)).to(device), 2, proj)
+    ones = torch.ones(D ** 3, device=device)
+    hitp = torch.empty_like(proj)
+    nh.project(geom, ones, 1, hitp)
+    torch.cuda.synchronize()
+    clean = proj.view(g.n_views, -1).cpu().numpy()
+    hit = hitp.view(g.n_views, -1).cpu().numpy() > 0
+    a_meas = S.poisson_measure(clean, w.I0, seed + 1)
+    cands = [np.nonzero(hit[v])[0] for v in range(g.n_views)]
+    return geom, vol, a_meas, cands
+
+
+def run_ours(args, rank: int, world: int, local_rank: int):
+    import torch
+    from paper_2506_19742_gb300 import build as nhbuild
+    from paper_2506_19742_gb300 import nhcbct as nh
+
+    nhbuild.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def allmax(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    w = S.WORKLOADS[args.workload]
+    seed = args.seed + 1000 * rank
+    geom, vol, a_meas_all, cands = make_scan(nh, torch, w, seed, dev)
+    R, N = w.n_rays, w.n_samples
+    K, W = args.steps, args.warmup
+    rng = np.random.default_rng(seed + 2)
+
+    def make_batches(n):
+        out = []
+        for _ in range(n):
+            view, pix = S.pick_rays(rng, w.geometry.n_views, cands, R)
+            out.append((view, pix, a_meas_all[view][pix].astype(np.float32)))
+        return out
+
+    host_batches = make_batches(W + K)
+    dev_batches = [(v, torch.from_numpy(p).to(dev), torch.from_numpy(a).to(dev)) for v, p, a in host_batches]
+
+    def measure(wl: S.Workload):
+        field = nh.Field(wl.field, params=S.init_params(wl.field, seed))
+        ws = nh.workspace(nh.step_workspace_bytes(field, R, N), dev)
+        loss = torch.zeros(1, device=dev)
+        stream = torch.cuda.current_stream()
+        for v, p, a in dev_batches[:W]:
+            nh.train_step(field, geom, v, p, a, N, loss, ws)
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for v, p, a in dev_batches[W:]:
+            nh.train_step(field, geom, v, p, a, N, loss, ws)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return field, ws, e0.elapsed_time(e1)
+
+    phys = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[local_rank]
+               if os.environ.get("CUDA_VISIBLE_DEVICES") else local_rank)
+    with ClockSampler(phys) as clk:
+        field, ws, ms = measure(w)
+    clocks = clk.summary()
+    ms = allmax(ms)
+    samples_all = float(R * N * K * world)
+    value = samples_all / (ms / 1e3)
+
+    # per-kernel durations (CUDA events on the launching stream) for the roofline
+    stream = torch.cuda.current_stream()
+    a_pred = torch.empty(R, device=dev)
+    nk = min(K, 20)
+
+    def timed(fn):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nk)]
+        for i in range(nk):
+            evs[i][0].record(stream)
+            fn(i)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(b) for a, b in evs]))
+
+    dLdA = torch.full((R,), 1e-3, device=dev)
+    t_fwd = timed(lambda i: nh.render_forward(field, geom, dev_batches[W + i][0], dev_batches[W + i][1], N,
+                                              a_pred, ws))
+    t_bwd = timed(lambda i: nh.render_backward(field, geom, dev_batches[W + i][0], dev_batches[W + i][1], N,
+                                               dLdA, ws))
+    t_adam = timed(lambda i: nh.optimizer_step(field))
+    peaks, peak_kind = read_peaks()
+    tb = 4 if w.field.precision == S.PREC_F32 else 2
+    L, F = w.field.n_levels, w.field.n_feat
+    bytes_per_sample = L * 8 * F * tb + L * 8 * F * 4     # gather + scatter payload
+    achieved = bytes_per_sample * R * N / (t_bwd / 1e3) / 1e9
+    peak = peaks["hbm_gbs"]
+    roofline = {"kernel": "k_ray_backward", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": profiled_traffic("ray_backward", w.name),
+                "peak_source": f"{peak_kind} hbm_gbs",
+                "bytes_per_sample": bytes_per_sample, "units_per_launch": R * N,
+                "launch_ms": {"forward+sum": round(t_fwd, 4), "backward": round(t_bwd, 4),
+                              "adam": round(t_adam, 4)}}
+
+    # end to end through the host-buffer entry point (pinned host in, loss out)
+    pins = [(v, torch.from_numpy(p).pin_memory(), torch.from_numpy(a).pin_memory()) for v, p, a in host_batches]
+    loss_h = torch.zeros(1).pin_memory()
+    for v, p, a in pins[:W]:
+        nh.train_step_host(field, geom, v, p, a, N, loss_h, ws)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    losses = []
+    for v, p, a in pins[W:]:
+        nh.train_step_host(field, geom, v, p, a, N, loss_h, ws)
+        torch.cuda.current_stream().synchronize()      # read the step's loss on the host
+        losses.append(float(loss_h[0]))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = allmax(max(e0.elapsed_time(e1), (time.perf_counter() - t0) * 1e3))
+    e2e = {"value": samples_all / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": R * 4 + R * 4,
+           "d2h_bytes_per_step": 4}
+
+    mixed = None
+    if args.mixed and args.mixed != args.workload:
+        wm = S.WORKLOADS[args.mixed]
+        if wm.n_rays == R and wm.n_samples == N and wm.geometry == w.geometry:
+            _, _, ms_m = measure(wm)
+            ms_m = allmax(ms_m)
+            mixed = {"workload": wm.name, "value": samples_all / (ms_m / 1e3), "unit": UNIT,
+                     "ms_per_step": ms_m / K, "speedup_vs_fp32": (samples_all / (ms_m / 1e3)) / value}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, args.cpu_seconds, args.seed)
+
+    if dist is not None:
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    f = w.field
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if f.precision == S.PREC_F32 else ("bf16" if f.precision == S.PREC_BF16 else "f16"),
+        "data": "synthetic",
+        "config": {"workload": w.name, "rays_per_step": R, "samples_per_ray": N,
+                   "levels": f.n_levels, "features": f.n_feat, "log2_T": f.log2_T,
+                   "resolutions": [f.base_res, f.max_res], "norm": f.norm, "mlp": f"{f.hidden_layers}x{f.width}",
+                   "volume": w.vol_D, "views": w.geometry.n_views,
+                   "detector": [w.geometry.det_nu, w.geometry.det_nv],
+                   "l2": "working set larger than L2: each step's Adam streams "
+                         f"{4 * 4 * S.param_layout(f)['_total'][1] / 1e6:.0f} MB of parameter state",
+                   "parallelism": f"replicas x{world}"},
+        "clocks": clocks, "e2e": e2e, "gpu_launches": 5 * K, "roofline": roofline, "cpu_baseline": cpu,
+        "mixed": mixed, "final_loss": losses[-1] if losses else None,
+    }
+    print(json.dumps(line))
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    w = S.WORKLOADS[args.workload]
+    # one bounded oracle sample per step: about 2 s each keeps K + W steps within minutes
+    per_step = 2.0
+    for _ in range(args.warmup):
+        oracle_sample_rays(w, 0.1, args.seed)
+    t0 = time.perf_counter()
+    samples = 0.0
+    desc = ""
+    for k in range(args.steps):
+        n, _, desc = oracle_sample_rays(w, per_step, args.seed + k)
+        samples += n
+    el = time.perf_counter() - t0
+    value = samples / el
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": w.name, "rays_per_step": w.n_rays, "samples_per_ray": w.n_samples},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse_args()
+    if args.cpu_worker:
+        n, el, desc = oracle_sample_rays(S.WORKLOADS[args.workload], args.cpu_seconds, args.seed)
+        print(json.dumps({"value": n / el, "sample": desc}))
+        return
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,251 @@
+/*
+ * nhcbct.h - C ABI of the GB300 NeRF-CBCT training library (libnhcbct.so).
+ *
+ * The library trains the field of "NeRF-based CBCT Reconstruction needs
+ * Normalization and Initialization": a multiresolution hash encoder, the
+ * Normalized Hash Encoder (a LayerNorm between encoder and network, Sec. 2.3)
+ * and a small MLP that predicts attenuation mu(x, y, z). Cone-beam rays from a
+ * known source and detector (Sec. 2.2) are sampled, mu is integrated with the
+ * Beer-Lambert sum A = sum_i mu_i delta_i (Eq. 1), and the loss against the
+ * measured projections (Eq. 3) is backpropagated into the MLP and, by
+ * scatter-add, into the hash tables; Adam updates every parameter (Sec. 3.1).
+ * Mapping Consistency Initialization pre-trains the field on voxel values
+ * (Eq. 2, Sec. 2.4) and transfers only the LN and MLP weights (Sec. 2.1).
+ *
+ * Conventions
+ *  - Every device buffer is owned by the caller (allocate, e.g., with PyTorch and
+ *    pass the pointer). Handles own host metadata only; no call allocates or
+ *    frees device memory, and nothing on the training path synchronizes.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Device work is enqueued on it and completes asynchronously.
+ *  - Argument errors are reported synchronously as a negative nh_status and
+ *    nothing is enqueued. Device-side conditions (non-finite loss or gradients)
+ *    set flags that field_poll_status() reads; the optimizer then skips the step.
+ *  - Lengths are in units of the volume side: the volume is the unit cube
+ *    [0,1]^3 in normalized coordinates, so delta_i and A are dimensionless.
+ *  - All float arrays are IEEE binary32 unless stated otherwise; device pointers
+ *    must be 16-byte aligned, except the ray batch arrays (4-byte aligned).
+ *  - Functions are thread-safe for distinct handles; calls on one field must be
+ *    ordered by the caller (one stream, or events between streams).
+ */
+#ifndef NHCBCT_H
+#define NHCBCT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+typedef int32_t nh_status;
+#define NH_OK                  0
+#define NH_ERR_INVALID_ARG    -1  /* null handle/pointer, value out of range          */
+#define NH_ERR_CUDA           -2  /* a CUDA runtime call failed (see nh_last_error)   */
+#define NH_ERR_SIZE_MISMATCH  -3  /* buffer or workspace smaller than required        */
+#define NH_ERR_NONFINITE      -4  /* a non-finite value was detected; step skipped    */
+#define NH_ERR_TIMEOUT        -5  /* reserved: a bounded device wait gave up          */
+#define NH_ERR_UNSUPPORTED    -6  /* configuration valid but not compiled in          */
+#define NH_ERR_ALIGNMENT      -7  /* a device pointer is not suitably aligned         */
+
+/* Human-readable name of a status code (static string). */
+const char* nh_status_string(nh_status s);
+/* Copies the calling thread's last error detail into buf (NUL-terminated). */
+nh_status nh_last_error(char* buf, size_t n);
+/* Library ABI version (major * 100 + minor). */
+int32_t nh_version(void);
+
+/* ------------------------------------------------------------------ geometry
+ * Circular cone-beam scan about the volume's z axis (the source and detector
+ * positions are known, Sec. 2.2). View v is at angle
+ *   theta_v = angle0 + v * span / n_views,
+ * source s = c0 + (dso / side) (cos, sin, 0), detector centre
+ * c0 - ((dsd - dso) / side) (cos, sin, 0), detector axes u = (-sin, cos, 0) and
+ * v = (0, 0, 1), c0 = (1/2, 1/2, 1/2). Pixel id p = j * det_nu + i is the pixel
+ * of column i, row j, centred ((i + 1/2) - nu/2) du, ((j + 1/2) - nv/2) dv from
+ * the detector centre. Per-view constants are computed in double on the host and
+ * rounded once to float.
+ */
+typedef struct nh_geometry nh_geometry;
+typedef struct {
+    int32_t n_views;
+    double  angle0_rad, span_rad;
+    double  dso_mm, dsd_mm;          /* source-origin, source-detector distance */
+    int32_t det_nu, det_nv;          /* detector columns, rows                  */
+    double  det_du_mm, det_dv_mm;    /* pixel pitch                             */
+    double  vol_side_mm;             /* side of the cubic volume                */
+} nh_geometry_desc;
+
+nh_status geometry_create(const nh_geometry_desc* desc, nh_geometry** out);
+void      geometry_destroy(nh_geometry* g);
+/* Host copy of the per-view table: n_views rows of 12 floats (s, c, u, v), then
+ * du, dv (volume units). n_floats must be >= 12 * n_views + 2. */
+nh_status geometry_view_table(const nh_geometry* g, float* host_out, size_t n_floats);
+
+/* ------------------------------------------------------------------ field
+ * Hash grid: L levels, F features, T = 2^log2_T entries per level; level
+ * resolutions N_l = floor(base * exp(l (ln max - ln base) / (L - 1)) + 1e-9).
+ * A level with (N_l + 1)^3 <= T is indexed densely, otherwise by the spatial
+ * hash (x * 1) ^ (y * 2654435761) ^ (z * 805459861) mod T.
+ * Normalization (Sec. 2.3): per-point LayerNorm of the L*F features (one
+ * group, or one group per level), then affine gamma/beta and the channel mask.
+ * MLP: hidden_layers Linear+ReLU layers of `width`, Linear to 1, sigmoid.
+ *
+ * Flat parameter vector (float32, one buffer; also the layout of grads/adam_m/
+ * adam_v): tables [L][T][F] | gamma [D] | beta [D] | W_0 [width][D] | b_0 [width]
+ * | ... | W_H [1][width] | b_H [1], D = L * F, H = hidden_layers.
+ */
+#define NH_NORM_NONE          0
+#define NH_NORM_LN            1
+#define NH_NORM_LN_PER_LEVEL  2
+#define NH_PREC_F32   0   /* float32 tables, float32 FFMA MLP                     */
+#define NH_PREC_BF16  1   /* bf16 table copy + bf16 tensor-core MLP, f32 master   */
+#define NH_PREC_F16   2   /* f16 table copy + f16 tensor-core MLP, f32 master     */
+#define NH_LOSS_MSE   0   /* mean over rays of (A - A_meas)^2                      */
+#define NH_LOSS_L1    1   /* mean over rays of |A - A_meas| (Eq. 3)                */
+#define NH_PART_HASH  1u  /* export/import parts */
+#define NH_PART_LN    2u
+#define NH_PART_MLP   4u
+#define NH_PART_ADAM  8u  /* Adam moments of the selected parts */
+#define NH_FLAG_NONFINITE 1u  /* a kernel saw a non-finite loss or gradient */
+#define NH_FLAG_SKIPPED   2u  /* the last optimizer step was skipped        */
+
+typedef struct nh_field nh_field;
+typedef struct {
+    int32_t n_levels, n_feat, log2_T, base_res, max_res;
+    int32_t norm;               /* NH_NORM_*                                      */
+    float   ln_eps;
+    int32_t hidden_layers, width;
+    int32_t precision;          /* NH_PREC_*                                      */
+    int32_t loss;               /* NH_LOSS_*                                      */
+    float   lr, beta1, beta2, adam_eps;
+    float   loss_scale_init;    /* 1 for f32/bf16; e.g. 1024 for f16              */
+    int32_t growth_interval;    /* 0: static loss scale; else double after this
+                                   many finite steps, halve on overflow           */
+} nh_field_desc;
+
+typedef struct {
+    uint64_t n_params;          /* floats in the flat parameter vector */
+    uint64_t n_table_params;    /* L * T * F (first in the vector)     */
+    uint64_t off_gamma, off_beta, off_mlp;   /* float offsets          */
+    uint64_t bytes_params, bytes_grads, bytes_adam_m, bytes_adam_v;
+    uint64_t bytes_tables_lp;   /* 0 for NH_PREC_F32                    */
+    uint64_t bytes_state;       /* small device state block            */
+} nh_field_sizes;
+
+typedef struct {
+    float* params;              /* bytes_params, float32 master weights        */
+    float* grads;               /* bytes_grads; zero it with field_reset_state */
+    float* adam_m;
+    float* adam_v;
+    void*  tables_lp;           /* bf16/f16 copy of the tables, or NULL (f32)  */
+    void*  state;               /* bytes_state                                 */
+} nh_field_buffers;
+
+/* Sizes of every caller-owned buffer for this configuration. */
+nh_status field_query_sizes(const nh_field_desc* desc, nh_field_sizes* out);
+/* Binds a handle to caller-owned buffers (not initialised: see field_reset_state). */
+nh_status field_create(const nh_field_desc* desc, const nh_field_buffers* buf, nh_field** out);
+void      field_destroy(nh_field* f);                 /* never frees caller memory */
+/* Zeroes grads, Adam moments, step count and flags; loss scale = init; channel
+ * mask = ones; refreshes the low-precision table copy from params. */
+nh_status field_reset_state(nh_field* f, void* stream);
+/* Refreshes the low-precision table copy after the caller wrote params. */
+nh_status field_refresh_lowp(nh_field* f, void* stream);
+/* Channel mask m (Sec. 2.3: masking of noisy feature channels), n = L * F host floats. */
+nh_status field_set_channel_mask(nh_field* f, const float* mask_host, int32_t n, void* stream);
+nh_status field_level_resolutions(const nh_field* f, int32_t* out, int32_t n);
+/* Export / import a subset of the parameters (MCI transfers NH_PART_LN |
+ * NH_PART_MLP, Sec. 2.1). The packed order is HASH, LN (gamma, beta), MLP, then,
+ * with NH_PART_ADAM, adam_m and adam_v of the same parts. Device-to-device. */
+nh_status field_export_bytes(const nh_field* f, uint32_t parts, size_t* out);
+nh_status field_export(const nh_field* f, uint32_t parts, void* dev_dst, size_t n_bytes, void* stream);
+nh_status field_import(nh_field* f, uint32_t parts, const void* dev_src, size_t n_bytes, void* stream);
+/* Synchronizes the stream and reads the state block: flags of the last optimizer
+ * step (NH_FLAG_*), current loss scale, Adam step count. Any pointer may be NULL. */
+nh_status field_poll_status(nh_field* f, void* stream, uint32_t* flags, float* loss_scale,
+                            int32_t* step);
+
+/* ------------------------------------------------------------------ training
+ * A ray batch: one view, n_rays detector pixels (Sec. 3.1: one view per batch,
+ * rays per view), n_samples midpoint samples per ray along [near, far] of the
+ * ray's intersection with the volume (delta = (far - near) / n_samples). Rays
+ * that miss the volume predict A = 0 and contribute no gradient.
+ * pix: device int32[n_rays]; a_meas: device float[n_rays] (may be NULL where unused).
+ */
+typedef struct {
+    int32_t        view;
+    int32_t        n_rays;
+    const int32_t* pix;
+    const float*   a_meas;
+    int32_t        n_samples;
+} nh_ray_batch;
+
+/* Workspace bytes needed by train_step / render_* / fit_points_step for a batch. */
+nh_status step_workspace_bytes(const nh_field* f, int32_t n_rays, int32_t n_samples, size_t* out);
+
+/* One training step: render (Eq. 1), loss vs a_meas (MSE or L1, Eq. 3) written to
+ * loss_dev[0] (device float), backward into grads, Adam (Sec. 3.1). */
+nh_status train_step(nh_field* f, const nh_geometry* g, const nh_ray_batch* b, float* loss_dev,
+                     void* ws, size_t ws_bytes, void* stream);
+/* The same step from HOST arrays (pinned memory for asynchrony): pix_host and
+ * a_meas_host are copied into the workspace, and the loss is copied back to
+ * loss_host, valid once the stream has synchronized. */
+nh_status train_step_host(nh_field* f, const nh_geometry* g, int32_t view, int32_t n_rays,
+                          const int32_t* pix_host, const float* a_meas_host, int32_t n_samples,
+                          float* loss_host, void* ws, size_t ws_bytes, void* stream);
+/* Forward only: a_pred_dev[r] = sum_i mu_i delta_i (Eq. 1). */
+nh_status render_forward(const nh_field* f, const nh_geometry* g, const nh_ray_batch* b,
+                         float* a_pred_dev, void* ws, size_t ws_bytes, void* stream);
+/* Backward only: ACCUMULATES into grads the gradient of sum_r dLdA[r] * A_r
+ * (features are recomputed, not stored). No optimizer step. */
+nh_status render_backward(nh_field* f, const nh_geometry* g, const nh_ray_batch* b,
+                          const float* dLdA_dev, void* ws, size_t ws_bytes, void* stream);
+/* Adam over every parameter with the accumulated grads, then zeroes grads. */
+nh_status optimizer_step(nh_field* f, void* stream);
+
+/* MCI pre-training step (Eq. 2): loss = mean |mu_gt - M(x)| over n_pts points
+ * xyz_dev (float[3 * n_pts], normalized coordinates), written to loss_dev[0];
+ * backward and Adam as in train_step. */
+nh_status fit_points_step(nh_field* f, int32_t n_pts, const float* xyz_dev, const float* mu_gt_dev,
+                          float* loss_dev, void* ws, size_t ws_bytes, void* stream);
+/* The voxel-loss forward and backward of fit_points_step without the optimizer:
+ * ACCUMULATES the gradient of the Eq. 2 loss into grads and writes the loss. */
+nh_status fit_points_backward(nh_field* f, int32_t n_pts, const float* xyz_dev, const float* mu_gt_dev,
+                              float* loss_dev, void* ws, size_t ws_bytes, void* stream);
+/* Workspace bytes for fit_points_step / fit_points_backward. */
+nh_status points_workspace_bytes(const nh_field* f, int32_t n_pts, size_t* out);
+
+/* ------------------------------------------------------------------ evaluation
+ * mu = M(x) at n points (float[3n] in, float[n] out). */
+nh_status query_points(const nh_field* f, int32_t n, const float* xyz_dev, float* mu_dev, void* stream);
+/* mu at the D^3 voxel centres ((k + 1/2) / D), out_dev float[D^3] in [z][y][x] order. */
+nh_status query_volume(const nh_field* f, int32_t D, float* out_dev, void* stream);
+
+/* ------------------------------------------------------------------ data synthesis
+ * Forward projection of a voxel volume (the TIGRE projections of Sec. 3.1):
+ * for every view and pixel, the clipped ray is cut into
+ * n = ceil((far - near) * D * oversample) equal steps and the trilinearly
+ * interpolated volume (voxel centres at (k + 1/2) / D, zero outside) is summed
+ * at the step midpoints times the step. vol_dev float[D^3] [z][y][x];
+ * proj_dev float[n_views * det_nv * det_nu] [view][row][col]. */
+nh_status project(const nh_geometry* g, const float* vol_dev, int32_t D, int32_t oversample,
+                  float* proj_dev, void* stream);
+
+/* ------------------------------------------------------------------ stage probes
+ * The individual stages of the fused kernels, exposed for bitwise tests.
+ * sample_rays: positions float[3 * n_rays * n_samples] ([ray][sample][xyz]) and
+ * delta float[n_rays] of the ray sampler. */
+nh_status sample_rays(const nh_geometry* g, int32_t view, int32_t n_rays, const int32_t* pix_dev,
+                      int32_t n_samples, float* xyz_dev, float* delta_dev, void* stream);
+/* hash_corners: for n points, corner indices uint32[n][L][8] and weights float[n][L][8]. */
+nh_status hash_corners(const nh_field* f, int32_t n, const float* xyz_dev, uint32_t* idx_dev,
+                       float* w_dev, void* stream);
+/* encode_points: trilinear hash features float[n][L * F] (the gather stage). */
+nh_status encode_points(const nh_field* f, int32_t n, const float* xyz_dev, float* h_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NHCBCT_H */

@@ -1,0 +1,179 @@
+// Adam over the whole flat parameter vector (Sec. 3.1: Adam, lr 1e-3) with the
+// float32 master copy, the bf16 / f16 working copy of the tables, dynamic loss
+// scaling and the non-finite step skip.
+//
+//  k_adam_prep  one thread: reads the step's flags, decides skip / apply, updates
+//               the loss scale and step count, computes the bias corrections.
+//  k_adam       grid-stride float4 pass: m, v, p updated in place (torch.optim.Adam
+//               semantics: bias-corrected, eps outside the square root), grads
+//               zeroed, low-precision table copy refreshed. A skipped step only
+//               zeroes the grads.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "nh_internal.h"
+
+namespace nh {
+
+__global__ void k_adam_prep(DeviceState* st, float lr, float beta1, float beta2, int growth) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const uint32_t flags = st->flags;
+    const bool skip = (flags & NH_FLAG_NONFINITE) != 0u;
+    st->flags = 0u;
+    st->inv_scale = 1.f / st->loss_scale;
+    if (skip) {
+        st->skip = 1u;
+        st->last_flags = flags | NH_FLAG_SKIPPED;
+        if (growth > 0) {
+            st->loss_scale = fmaxf(st->loss_scale * 0.5f, 1.f);
+            st->good_steps = 0;
+        }
+        return;
+    }
+    st->skip = 0u;
+    st->last_flags = flags;
+    const int t = st->step + 1;
+    st->step = t;
+    st->step_size = lr / (1.f - powf(beta1, (float)t));
+    st->inv_bc2_sqrt = 1.f / sqrtf(1.f - powf(beta2, (float)t));
+    if (growth > 0) {
+        if (++st->good_steps >= growth) {
+            st->loss_scale = st->loss_scale * 2.f;
+            st->good_steps = 0;
+        }
+    }
+}
+
+template <typename LP>
+__device__ __forceinline__ void store_lp(LP* lp, int64_t i, float4 p);
+template <>
+__device__ __forceinline__ void store_lp<__nv_bfloat16>(__nv_bfloat16* lp, int64_t i, float4 p) {
+    __nv_bfloat162 a = __floats2bfloat162_rn(p.x, p.y), b = __floats2bfloat162_rn(p.z, p.w);
+    uint2 u;
+    u.x = *reinterpret_cast<unsigned int*>(&a);
+    u.y = *reinterpret_cast<unsigned int*>(&b);
+    *reinterpret_cast<uint2*>(lp + i) = u;
+}
+template <>
+__device__ __forceinline__ void store_lp<__half>(__half* lp, int64_t i, float4 p) {
+    __half2 a = __floats2half2_rn(p.x, p.y), b = __floats2half2_rn(p.z, p.w);
+    uint2 u;
+    u.x = *reinterpret_cast<unsigned int*>(&a);
+    u.y = *reinterpret_cast<unsigned int*>(&b);
+    *reinterpret_cast<uint2*>(lp + i) = u;
+}
+template <>
+__device__ __forceinline__ void store_lp<float>(float*, int64_t, float4) {}
+
+__device__ __forceinline__ float adam1(float& p, float& m, float& v, float g, float b1, float b2,
+                                       float eps, float step_size, float inv_bc2_sqrt) {
+    m = fmaf(b1, m, (1.f - b1) * g);
+    v = fmaf(b2, v, (1.f - b2) * g * g);
+    p = p - step_size * m / (sqrtf(v) * inv_bc2_sqrt + eps);
+    return p;
+}
+
+// n must be a multiple of 4; n_lp (a multiple of 4) leading entries refresh lp.
+template <typename LP>
+__global__ void __launch_bounds__(256) k_adam(float* __restrict__ p, float* __restrict__ g,
+                                              float* __restrict__ m, float* __restrict__ v, int64_t n,
+                                              LP* __restrict__ lp, int64_t n_lp, const DeviceState* st,
+                                              float b1, float b2, float eps) {
+    const bool skip = st->skip != 0u;
+    const float inv_scale = st->inv_scale, step_size = st->step_size, ib2 = st->inv_bc2_sqrt;
+    const int64_t n4 = n >> 2;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        float4 gg = reinterpret_cast<float4*>(g)[q];
+        reinterpret_cast<float4*>(g)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (skip) continue;
+        float4 pp = reinterpret_cast<float4*>(p)[q];
+        float4 mm = reinterpret_cast<float4*>(m)[q];
+        float4 vv = reinterpret_cast<float4*>(v)[q];
+        adam1(pp.x, mm.x, vv.x, gg.x * inv_scale, b1, b2, eps, step_size, ib2);
+        adam1(pp.y, mm.y, vv.y, gg.y * inv_scale, b1, b2, eps, step_size, ib2);
+        adam1(pp.z, mm.z, vv.z, gg.z * inv_scale, b1, b2, eps, step_size, ib2);
+        adam1(pp.w, mm.w, vv.w, gg.w * inv_scale, b1, b2, eps, step_size, ib2);
+        reinterpret_cast<float4*>(p)[q] = pp;
+        reinterpret_cast<float4*>(m)[q] = mm;
+        reinterpret_cast<float4*>(v)[q] = vv;
+        if ((q << 2) < n_lp) store_lp<LP>(lp, q << 2, pp);
+    }
+}
+
+template <typename LP>
+__global__ void k_refresh(const float* __restrict__ p, LP* __restrict__ lp, int64_t n) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (n >> 2);
+         q += (int64_t)gridDim.x * blockDim.x)
+        store_lp<LP>(lp, q << 2, reinterpret_cast<const float4*>(p)[q]);
+}
+
+__global__ void k_init_state(DeviceState* st, float loss_scale) {
+    const int t = threadIdx.x;
+    if (t == 0) {
+        st->step = 0;
+        st->loss_scale = loss_scale;
+        st->good_steps = 0;
+        st->flags = 0u;
+        st->last_flags = 0u;
+        st->skip = 0u;
+        st->step_size = 0.f;
+        st->inv_bc2_sqrt = 1.f;
+        st->inv_scale = 1.f / loss_scale;
+        st->loss_accum = 0.f;
+    }
+    if (t < kMaxD) st->mask[t] = 1.f;
+}
+
+static int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+cudaError_t launch_adam(const FieldArgs& fa, float* params, float* grads, float* m, float* v, int64_t n,
+                        float lr, float beta1, float beta2, float eps, int growth_interval,
+                        cudaStream_t st) {
+    k_adam_prep<<<1, 32, 0, st>>>(fa.state, lr, beta1, beta2, growth_interval);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t n4 = n >> 2;
+    int64_t blocks = (n4 + 255) / 256;
+    const int64_t cap = (int64_t)sm_count() * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    if (fa.precision == NH_PREC_BF16)
+        k_adam<__nv_bfloat16><<<(unsigned)blocks, 256, 0, st>>>(params, grads, m, v, n,
+            (__nv_bfloat16*)fa.tables_lp, fa.n_table, fa.state, beta1, beta2, eps);
+    else if (fa.precision == NH_PREC_F16)
+        k_adam<__half><<<(unsigned)blocks, 256, 0, st>>>(params, grads, m, v, n, (__half*)fa.tables_lp,
+            fa.n_table, fa.state, beta1, beta2, eps);
+    else
+        k_adam<float><<<(unsigned)blocks, 256, 0, st>>>(params, grads, m, v, n, nullptr, 0, fa.state,
+            beta1, beta2, eps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refresh_lowp(const float* params, void* lp, int64_t n, int precision, cudaStream_t st) {
+    if (n == 0 || lp == nullptr || precision == NH_PREC_F32) return cudaSuccess;
+    int64_t blocks = ((n >> 2) + 255) / 256;
+    if (blocks > (int64_t)sm_count() * 8) blocks = (int64_t)sm_count() * 8;
+    if (precision == NH_PREC_BF16)
+        k_refresh<__nv_bfloat16><<<(unsigned)blocks, 256, 0, st>>>(params, (__nv_bfloat16*)lp, n);
+    else
+        k_refresh<__half><<<(unsigned)blocks, 256, 0, st>>>(params, (__half*)lp, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_state(DeviceState* s, float loss_scale, cudaStream_t st) {
+    k_init_state<<<1, 64, 0, st>>>(s, loss_scale);
+    return cudaGetLastError();
+}
+
+}  // namespace nh

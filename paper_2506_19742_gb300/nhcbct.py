@@ -1,0 +1,412 @@
+"""Python binding of libnhcbct (ctypes): argument marshalling only.
+
+Every computation runs in the CUDA library; PyTorch supplies device memory and
+streams. The functions named like the C ABI (``train_step``, ``render_forward``,
+``query_volume``, ``project`` ...) take torch tensors and forward their device
+pointers and the current CUDA stream. ``Geometry`` and ``Field`` own the
+caller-side buffers the library asks for. Loading fails loudly if the built
+library is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnhcbct.so")
+
+NORM_NONE, NORM_LN, NORM_LN_PER_LEVEL = 0, 1, 2
+PREC_F32, PREC_BF16, PREC_F16 = 0, 1, 2
+LOSS_MSE, LOSS_L1 = 0, 1
+PART_HASH, PART_LN, PART_MLP, PART_ADAM = 1, 2, 4, 8
+FLAG_NONFINITE, FLAG_SKIPPED = 1, 2
+STATUS = {0: "NH_OK", -1: "NH_ERR_INVALID_ARG", -2: "NH_ERR_CUDA", -3: "NH_ERR_SIZE_MISMATCH",
+          -4: "NH_ERR_NONFINITE", -5: "NH_ERR_TIMEOUT", -6: "NH_ERR_UNSUPPORTED", -7: "NH_ERR_ALIGNMENT"}
+
+
+class NHError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {detail}")
+        self.status = status
+
+
+class GeometryDesc(C.Structure):
+    _fields_ = [("n_views", C.c_int32), ("angle0_rad", C.c_double), ("span_rad", C.c_double),
+                ("dso_mm", C.c_double), ("dsd_mm", C.c_double), ("det_nu", C.c_int32),
+                ("det_nv", C.c_int32), ("det_du_mm", C.c_double), ("det_dv_mm", C.c_double),
+                ("vol_side_mm", C.c_double)]
+
+
+class FieldDesc(C.Structure):
+    _fields_ = [("n_levels", C.c_int32), ("n_feat", C.c_int32), ("log2_T", C.c_int32),
+                ("base_res", C.c_int32), ("max_res", C.c_int32), ("norm", C.c_int32),
+                ("ln_eps", C.c_float), ("hidden_layers", C.c_int32), ("width", C.c_int32),
+                ("precision", C.c_int32), ("loss", C.c_int32), ("lr", C.c_float),
+                ("beta1", C.c_float), ("beta2", C.c_float), ("adam_eps", C.c_float),
+                ("loss_scale_init", C.c_float), ("growth_interval", C.c_int32)]
+
+
+class FieldSizes(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in (
+        "n_params", "n_table_params", "off_gamma", "off_beta", "off_mlp", "bytes_params",
+        "bytes_grads", "bytes_adam_m", "bytes_adam_v", "bytes_tables_lp", "bytes_state")]
+
+
+class FieldBuffers(C.Structure):
+    _fields_ = [("params", C.c_void_p), ("grads", C.c_void_p), ("adam_m", C.c_void_p),
+                ("adam_v", C.c_void_p), ("tables_lp", C.c_void_p), ("state", C.c_void_p)]
+
+
+class RayBatch(C.Structure):
+    _fields_ = [("view", C.c_int32), ("n_rays", C.c_int32), ("pix", C.c_void_p),
+                ("a_meas", C.c_void_p), ("n_samples", C.c_int32)]
+
+
+_P = C.c_void_p
+_I = C.c_int32
+_SZ = C.c_size_t
+_SIGS = {
+    "nh_status_string": (C.c_char_p, [_I]),
+    "nh_last_error": (_I, [C.c_char_p, _SZ]),
+    "nh_version": (_I, []),
+    "geometry_create": (_I, [C.POINTER(GeometryDesc), C.POINTER(_P)]),
+    "geometry_destroy": (None, [_P]),
+    "geometry_view_table": (_I, [_P, C.POINTER(C.c_float), _SZ]),
+    "field_query_sizes": (_I, [C.POINTER(FieldDesc), C.POINTER(FieldSizes)]),
+    "field_create": (_I, [C.POINTER(FieldDesc), C.POINTER(FieldBuffers), C.POINTER(_P)]),
+    "field_destroy": (None, [_P]),
+    "field_reset_state": (_I, [_P, _P]),
+    "field_refresh_lowp": (_I, [_P, _P]),
+    "field_set_channel_mask": (_I, [_P, C.POINTER(C.c_float), _I, _P]),
+    "field_level_resolutions": (_I, [_P, C.POINTER(_I), _I]),
+    "field_export_bytes": (_I, [_P, C.c_uint32, C.POINTER(_SZ)]),
+    "field_export": (_I, [_P, C.c_uint32, _P, _SZ, _P]),
+    "field_import": (_I, [_P, C.c_uint32, _P, _SZ, _P]),
+    "field_poll_status": (_I, [_P, _P, C.POINTER(C.c_uint32), C.POINTER(C.c_float), C.POINTER(_I)]),
+    "step_workspace_bytes": (_I, [_P, _I, _I, C.POINTER(_SZ)]),
+    "points_workspace_bytes": (_I, [_P, _I, C.POINTER(_SZ)]),
+    "train_step": (_I, [_P, _P, C.POINTER(RayBatch), _P, _P, _SZ, _P]),
+    "train_step_host": (_I, [_P, _P, _I, _I, _P, _P, _I, _P, _P, _SZ, _P]),
+    "render_forward": (_I, [_P, _P, C.POINTER(RayBatch), _P, _P, _SZ, _P]),
+    "render_backward": (_I, [_P, _P, C.POINTER(RayBatch), _P, _P, _SZ, _P]),
+    "optimizer_step": (_I, [_P, _P]),
+    "fit_points_step": (_I, [_P, _I, _P, _P, _P, _P, _SZ, _P]),
+    "fit_points_backward": (_I, [_P, _I, _P, _P, _P, _P, _SZ, _P]),
+    "query_points": (_I, [_P, _I, _P, _P, _P]),
+    "query_volume": (_I, [_P, _I, _P, _P]),
+    "project": (_I, [_P, _P, _I, _I, _P, _P]),
+    "sample_rays": (_I, [_P, _I, _I, _P, _I, _P, _P, _P]),
+    "hash_corners": (_I, [_P, _I, _P, _P, _P, _P]),
+    "encode_points": (_I, [_P, _I, _P, _P, _P]),
+}
+EXPORTS = tuple(_SIGS)
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads libnhcbct.so (built by ``paper_2506_19742_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libnhcbct.so not found at {path}: build it with "
+                           "`python -m paper_2506_19742_gb300.build` (no CPU fallback exists)")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        buf = C.create_string_buffer(512)
+        load().nh_last_error(buf, 512)
+        raise NHError(status, where, buf.value.decode(errors="replace"))
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dev(t, dtype, name):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError(f"{name}: expected a contiguous CUDA {dtype} tensor")
+    return t
+
+
+# ---------------------------------------------------------------------------- handles
+class Geometry:
+    """Cone-beam scan geometry (host metadata only)."""
+
+    def __init__(self, n_views=50, angle0_rad=0.0, span_rad=2 * 3.141592653589793, dso_mm=1000.0,
+                 dsd_mm=1500.0, det_nu=64, det_nv=64, det_du_mm=None, det_dv_mm=None,
+                 vol_side_mm=256.0, det_side_mm=700.0):
+        lib = load()
+        du = det_side_mm / det_nu if det_du_mm is None else det_du_mm
+        dv = det_side_mm / det_nv if det_dv_mm is None else det_dv_mm
+        self.desc = GeometryDesc(n_views, angle0_rad, span_rad, dso_mm, dsd_mm, det_nu, det_nv, du, dv,
+                                 vol_side_mm)
+        h = C.c_void_p()
+        _check(lib.geometry_create(C.byref(self.desc), C.byref(h)), "geometry_create")
+        self.handle = h
+        self.n_views, self.nu, self.nv = n_views, det_nu, det_nv
+
+    @classmethod
+    def from_config(cls, g):
+        return cls(g.n_views, g.angle0_rad, g.span_rad, g.dso_mm, g.dsd_mm, g.det_nu, g.det_nv,
+                   g.det_du_mm, g.det_dv_mm, g.vol_side_mm)
+
+    def view_table(self):
+        n = 12 * self.n_views + 2
+        buf = (C.c_float * n)()
+        _check(load().geometry_view_table(self.handle, buf, n), "geometry_view_table")
+        import numpy as np
+        a = np.frombuffer(buf, dtype=np.float32).copy()
+        return a[:-2].reshape(self.n_views, 12), a[-2], a[-1]
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.geometry_destroy(self.handle)
+            self.handle = None
+
+
+class Field:
+    """Hash grid + Normalized Hash Encoder + MLP with its caller-owned device buffers."""
+
+    def __init__(self, cfg, device="cuda", params=None):
+        lib = load()
+        self.cfg = cfg
+        self.desc = FieldDesc(cfg.n_levels, cfg.n_feat, cfg.log2_T, cfg.base_res, cfg.max_res, cfg.norm,
+                              cfg.ln_eps, cfg.hidden_layers, cfg.width, cfg.precision, cfg.loss, cfg.lr,
+                              cfg.beta1, cfg.beta2, cfg.adam_eps, cfg.loss_scale_init, cfg.growth_interval)
+        self.sizes = FieldSizes()
+        _check(lib.field_query_sizes(C.byref(self.desc), C.byref(self.sizes)), "field_query_sizes")
+        nf = self.sizes.bytes_params // 4
+        self.params = torch.zeros(nf, dtype=torch.float32, device=device)
+        self.grads = torch.zeros(nf, dtype=torch.float32, device=device)
+        self.adam_m = torch.zeros(nf, dtype=torch.float32, device=device)
+        self.adam_v = torch.zeros(nf, dtype=torch.float32, device=device)
+        lp = self.sizes.bytes_tables_lp
+        lp_dtype = torch.bfloat16 if cfg.precision == PREC_BF16 else torch.float16
+        self.tables_lp = torch.zeros(lp // 2, dtype=lp_dtype, device=device) if lp else None
+        self.state = torch.zeros(self.sizes.bytes_state // 4, dtype=torch.float32, device=device)
+        self.buffers = FieldBuffers(self.params.data_ptr(), self.grads.data_ptr(), self.adam_m.data_ptr(),
+                                    self.adam_v.data_ptr(),
+                                    self.tables_lp.data_ptr() if self.tables_lp is not None else None,
+                                    self.state.data_ptr())
+        h = C.c_void_p()
+        _check(lib.field_create(C.byref(self.desc), C.byref(self.buffers), C.byref(h)), "field_create")
+        self.handle = h
+        self.n_params = int(self.sizes.n_params)
+        if params is not None:
+            self.load_params(params)
+        else:
+            self.reset_state()
+
+    def load_params(self, flat):
+        """Copies a flat float32 parameter vector in and resets the optimizer state."""
+        t = torch.as_tensor(flat, dtype=torch.float32)
+        self.params[: self.n_params].copy_(t.to(self.params.device))
+        self.reset_state()
+
+    def reset_state(self, stream=None):
+        _check(load().field_reset_state(self.handle, _stream(stream)), "field_reset_state")
+
+    def refresh_lowp(self, stream=None):
+        _check(load().field_refresh_lowp(self.handle, _stream(stream)), "field_refresh_lowp")
+
+    def set_channel_mask(self, mask, stream=None):
+        import numpy as np
+        m = np.ascontiguousarray(mask, dtype=np.float32)
+        _check(load().field_set_channel_mask(self.handle, m.ctypes.data_as(C.POINTER(C.c_float)), len(m),
+                                             _stream(stream)), "field_set_channel_mask")
+
+    def level_resolutions(self):
+        out = (C.c_int32 * 32)()
+        _check(load().field_level_resolutions(self.handle, out, 32), "field_level_resolutions")
+        return list(out[: self.cfg.n_levels])
+
+    def poll_status(self, stream=None):
+        flags, scale, step = C.c_uint32(), C.c_float(), C.c_int32()
+        _check(load().field_poll_status(self.handle, _stream(stream), C.byref(flags), C.byref(scale),
+                                        C.byref(step)), "field_poll_status")
+        return flags.value, scale.value, step.value
+
+    def export_bytes(self, parts):
+        n = C.c_size_t()
+        _check(load().field_export_bytes(self.handle, parts, C.byref(n)), "field_export_bytes")
+        return n.value
+
+    def export(self, parts, stream=None):
+        out = torch.empty(self.export_bytes(parts) // 4, dtype=torch.float32, device=self.params.device)
+        _check(load().field_export(self.handle, parts, _ptr(out), out.numel() * 4, _stream(stream)),
+               "field_export")
+        return out
+
+    def import_(self, parts, blob, stream=None):
+        blob = _dev(blob, torch.float32, "blob")
+        _check(load().field_import(self.handle, parts, _ptr(blob), blob.numel() * 4, _stream(stream)),
+               "field_import")
+
+    def flat_params(self):
+        return self.params[: self.n_params]
+
+    def flat_grads(self):
+        return self.grads[: self.n_params]
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.field_destroy(self.handle)
+            self.handle = None
+
+
+# ---------------------------------------------------------------------------- workspaces
+def step_workspace_bytes(field: Field, n_rays: int, n_samples: int) -> int:
+    n = C.c_size_t()
+    _check(load().step_workspace_bytes(field.handle, n_rays, n_samples, C.byref(n)), "step_workspace_bytes")
+    return n.value
+
+
+def points_workspace_bytes(field: Field, n_pts: int) -> int:
+    n = C.c_size_t()
+    _check(load().points_workspace_bytes(field.handle, n_pts, C.byref(n)), "points_workspace_bytes")
+    return n.value
+
+
+def workspace(nbytes: int, device="cuda"):
+    """A 256-byte aligned device workspace (torch allocations are 512-byte aligned)."""
+    return torch.empty(max(1, (nbytes + 3) // 4), dtype=torch.float32, device=device)
+
+
+def _batch(view, pix, a_meas, n_samples):
+    pix = _dev(pix, torch.int32, "pix")
+    a_meas = _dev(a_meas, torch.float32, "a_meas")
+    n = 0 if pix is None else pix.numel()
+    return RayBatch(int(view), n, pix.data_ptr() if pix is not None else None,
+                    a_meas.data_ptr() if a_meas is not None else None, int(n_samples))
+
+
+# ---------------------------------------------------------------------------- entry points
+def train_step(field, geom, view, pix, a_meas, n_samples, loss_out, ws, stream=None):
+    b = _batch(view, pix, a_meas, n_samples)
+    _check(load().train_step(field.handle, geom.handle, C.byref(b), _ptr(loss_out), _ptr(ws),
+                             ws.numel() * 4, _stream(stream)), "train_step")
+
+
+def train_step_host(field, geom, view, pix_host, a_meas_host, n_samples, loss_host, ws, stream=None):
+    """pix_host (int32), a_meas_host (float32), loss_host (float32[1]): CPU tensors, ideally pinned."""
+    for t, dt in ((pix_host, torch.int32), (a_meas_host, torch.float32), (loss_host, torch.float32)):
+        if t.is_cuda or t.dtype != dt or not t.is_contiguous():
+            raise ValueError("train_step_host: expected contiguous host tensors")
+    _check(load().train_step_host(field.handle, geom.handle, int(view), pix_host.numel(), _ptr(pix_host),
+                                  _ptr(a_meas_host), int(n_samples), _ptr(loss_host), _ptr(ws),
+                                  ws.numel() * 4, _stream(stream)), "train_step_host")
+
+
+def render_forward(field, geom, view, pix, n_samples, a_pred, ws, stream=None):
+    b = _batch(view, pix, None, n_samples)
+    _check(load().render_forward(field.handle, geom.handle, C.byref(b), _ptr(a_pred), _ptr(ws),
+                                 ws.numel() * 4, _stream(stream)), "render_forward")
+
+
+def render_backward(field, geom, view, pix, n_samples, dLdA, ws, stream=None):
+    b = _batch(view, pix, None, n_samples)
+    _check(load().render_backward(field.handle, geom.handle, C.byref(b), _ptr(dLdA), _ptr(ws),
+                                  ws.numel() * 4, _stream(stream)), "render_backward")
+
+
+def optimizer_step(field, stream=None):
+    _check(load().optimizer_step(field.handle, _stream(stream)), "optimizer_step")
+
+
+def fit_points_step(field, xyz, mu_gt, loss_out, ws, stream=None):
+    xyz = _dev(xyz, torch.float32, "xyz")
+    mu_gt = _dev(mu_gt, torch.float32, "mu_gt")
+    _check(load().fit_points_step(field.handle, mu_gt.numel(), _ptr(xyz), _ptr(mu_gt), _ptr(loss_out),
+                                  _ptr(ws), ws.numel() * 4, _stream(stream)), "fit_points_step")
+
+
+def fit_points_backward(field, xyz, mu_gt, loss_out, ws, stream=None):
+    xyz = _dev(xyz, torch.float32, "xyz")
+    mu_gt = _dev(mu_gt, torch.float32, "mu_gt")
+    _check(load().fit_points_backward(field.handle, mu_gt.numel(), _ptr(xyz), _ptr(mu_gt), _ptr(loss_out),
+                                      _ptr(ws), ws.numel() * 4, _stream(stream)), "fit_points_backward")
+
+
+def query_points(field, xyz, mu_out, stream=None):
+    xyz = _dev(xyz, torch.float32, "xyz")
+    _check(load().query_points(field.handle, mu_out.numel(), _ptr(xyz), _ptr(mu_out), _stream(stream)),
+           "query_points")
+
+
+def query_volume(field, D, out, stream=None):
+    _check(load().query_volume(field.handle, int(D), _ptr(out), _stream(stream)), "query_volume")
+
+
+def project(geom, vol, oversample, proj_out, stream=None):
+    vol = _dev(vol, torch.float32, "vol")
+    _check(load().project(geom.handle, _ptr(vol), vol.shape[0], int(oversample), _ptr(proj_out),
+                          _stream(stream)), "project")
+
+
+def sample_rays(geom, view, pix, n_samples, xyz_out, delta_out, stream=None):
+    pix = _dev(pix, torch.int32, "pix")
+    _check(load().sample_rays(geom.handle, int(view), pix.numel(), _ptr(pix), int(n_samples), _ptr(xyz_out),
+                              _ptr(delta_out), _stream(stream)), "sample_rays")
+
+
+def hash_corners(field, xyz, idx_out, w_out, stream=None):
+    xyz = _dev(xyz, torch.float32, "xyz")
+    _check(load().hash_corners(field.handle, xyz.numel() // 3, _ptr(xyz), _ptr(idx_out), _ptr(w_out),
+                               _stream(stream)), "hash_corners")
+
+
+def encode_points(field, xyz, h_out, stream=None):
+    xyz = _dev(xyz, torch.float32, "xyz")
+    _check(load().encode_points(field.handle, xyz.numel() // 3, _ptr(xyz), _ptr(h_out), _stream(stream)),
+           "encode_points")
+
+
+# ---------------------------------------------------------------------------- autograd
+class Render(torch.autograd.Function):
+    """A = render(params) through the hand-written CUDA forward and backward.
+
+    ``params`` is the field's flat parameter tensor; the backward recomputes the
+    features on the GPU and returns dL/dparams (gradients are not accumulated into
+    the field's optimizer buffers)."""
+
+    @staticmethod
+    def forward(ctx, params, field, geom, view, pix, n_samples):
+        ws = workspace(step_workspace_bytes(field, pix.numel(), n_samples), params.device)
+        a = torch.empty(pix.numel(), dtype=torch.float32, device=params.device)
+        render_forward(field, geom, view, pix, n_samples, a, ws)
+        ctx.save_for_backward(pix)
+        ctx.field, ctx.geom, ctx.view, ctx.n = field, geom, view, n_samples
+        return a
+
+    @staticmethod
+    def backward(ctx, dA):
+        (pix,) = ctx.saved_tensors
+        f = ctx.field
+        saved = f.grads.clone()
+        f.grads.zero_()
+        ws = workspace(step_workspace_bytes(f, pix.numel(), ctx.n), dA.device)
+        render_backward(f, ctx.geom, ctx.view, pix, ctx.n, dA.contiguous().float(), ws)
+        _, scale, _ = f.poll_status()
+        g = f.grads[: f.n_params].clone() / scale
+        f.grads.copy_(saved)
+        return g, None, None, None, None, None

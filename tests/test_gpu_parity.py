@@ -1,0 +1,342 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Tolerances (from the method's arithmetic and the stated targets): sample
+positions, deltas and corner indices bitwise; features and per-point mu 1e-5
+relative (float32 accumulation of <= 8 L terms and a 5-layer MLP); ray sums and
+losses 1e-5 relative; gradients 1e-3 relative (float32 accumulation in a
+different order, scatter atomics reorder sums).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as S
+from _cases import batch, field_cfg, hit_pixels, oracle_geom, replace, rounded_tables
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _t(a, dtype=None):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+GEOM = S.GeometryConfig(n_views=6, det_nu=40, det_nv=36)
+
+
+def _grad_close(g_gpu, g_orc, cfg, rtol=1e-3, what=""):
+    lay = S.param_layout(cfg)
+    for name in ("tables", "gamma", "beta") + tuple(f"{p}{k}" for k in range(cfg.hidden_layers + 1)
+                                                 for p in ("W", "b")):
+        o, n = lay[name]
+        a, b = g_gpu[o:o + n].astype(np.float64), g_orc[o:o + n]
+        scale = np.abs(b).max()
+        if scale == 0:
+            assert np.abs(a).max() == 0, (what, name)
+            continue
+        err = np.abs(a - b).max() / scale
+        assert err <= rtol, (what, name, err)
+
+
+# ------------------------------------------------------------------------------ stages
+@pytest.mark.parametrize("N", [1, 37, 64, 200])
+def test_sampler_positions_and_deltas_are_bitwise(lib, N):
+    geom = lib.Geometry.from_config(GEOM)
+    tab, du, dv = geom.view_table()
+    otab, odu, odv, nu, nv = oracle_geom(GEOM)
+    assert np.array_equal(tab.view(np.uint32), otab.view(np.uint32))
+    assert np.float32(du) == odu and np.float32(dv) == odv
+    pix = np.arange(nu * nv, dtype=np.int32)          # every pixel, hits and misses
+    for view in (0, 2, 5):
+        xyz = torch.empty(len(pix) * N * 3, device="cuda")
+        delta = torch.empty(len(pix), device="cuda")
+        lib.sample_rays(geom, view, _t(pix), N, xyz, delta)
+        o, d, near, far, hit = oracle.ray_setup(otab, odu, odv, nu, nv, view, pix)
+        x, dl = oracle.sample_points(o, d, near, far, N)
+        g = _np(xyz).reshape(len(pix), N, 3)
+        assert np.array_equal(_np(delta).view(np.uint32), dl.view(np.uint32))
+        assert np.array_equal(g[hit].view(np.uint32), x[hit].view(np.uint32))
+
+
+@pytest.mark.parametrize("L,log2T,base,top", [(8, 12, 4, 48), (16, 8, 2, 512), (8, 20, 16, 64)])
+def test_corner_indices_are_bitwise(lib, L, log2T, base, top):
+    cfg = field_cfg(n_levels=L, log2_T=log2T, base_res=base, max_res=top)
+    field = lib.Field(cfg, params=S.init_params(cfg, 0))
+    assert field.level_resolutions() == oracle.level_resolutions(L, base, top)
+    rng = np.random.default_rng(L + log2T)
+    pts = rng.random((3000, 3)).astype(np.float32)
+    pts[:8] = [[0, 0, 0], [1, 1, 1], [1, 0, 0.5], [0.5, 0.5, 0.5], [-0.1, 0.3, 1.2],
+               [np.float32(1) - np.float32(2 ** -24), 0.25, 0.75], [0.125, 0.5, 0.875], [1e-30, 0.9999, 0.5]]
+    idx = torch.empty(len(pts) * L * 8, dtype=torch.int32, device="cuda")
+    w = torch.empty(len(pts) * L * 8, device="cuda")
+    lib.hash_corners(field, _t(pts), idx, w)
+    oi, ow, _ = oracle.corners(pts, oracle.level_resolutions(L, base, top), 1 << log2T)
+    assert np.array_equal(_np(idx).view(np.uint32).reshape(oi.shape), oi)
+    np.testing.assert_allclose(_np(w).reshape(ow.shape), ow, rtol=0, atol=2e-7)
+
+
+@pytest.mark.parametrize("precision", [S.PREC_F32, S.PREC_BF16, S.PREC_F16])
+def test_gather_features_match_oracle(lib, precision):
+    cfg = field_cfg(n_levels=16, log2_T=10, base_res=3, max_res=300, precision=precision)
+    flat = S.init_params(cfg, 1, table_scale=1.0)
+    field = lib.Field(cfg, params=flat)
+    pts = np.random.default_rng(5).random((4097, 3)).astype(np.float32)
+    h = torch.empty(len(pts) * cfg.d_in, device="cuda")
+    lib.encode_points(field, _t(pts), h)
+    ref_flat = rounded_tables(flat, cfg, precision)
+    tables = oracle.unflatten(ref_flat.astype(np.float64), cfg)["tables"]
+    ref = oracle.encode(pts, tables, oracle.level_resolutions(16, 3, 300), cfg.T)
+    np.testing.assert_allclose(_np(h).reshape(ref.shape), ref, rtol=0, atol=1e-5 * np.abs(ref).max())
+
+
+# ------------------------------------------------------------------------------ forward
+FWD_CASES = [
+    dict(norm=S.NORM_LN, n_levels=16, hidden_layers=4, log2_T=12, max_res=200),
+    dict(norm=S.NORM_LN_PER_LEVEL, n_levels=8, hidden_layers=2),
+    dict(norm=S.NORM_NONE, n_levels=8, hidden_layers=1, log2_T=8),
+    dict(norm=S.NORM_LN, n_levels=16, hidden_layers=3, log2_T=16, max_res=1024),
+]
+
+
+@pytest.mark.parametrize("case", range(len(FWD_CASES)))
+@pytest.mark.parametrize("N", [45, 64])
+def test_render_forward_matches_oracle(lib, case, N):
+    cfg = field_cfg(**FWD_CASES[case])
+    flat = S.init_params(cfg, 10 + case, table_scale=0.5)
+    field = lib.Field(cfg, params=flat)
+    mask = np.ones(cfg.d_in, dtype=np.float32)
+    mask[3] = 0.0
+    field.set_channel_mask(mask)
+    geom = lib.Geometry.from_config(GEOM)
+    pix = batch(GEOM, 4, 300, seed=case, n_miss=5)
+    ws = lib.workspace(lib.step_workspace_bytes(field, len(pix), N))
+    a = torch.empty(len(pix), device="cuda")
+    lib.render_forward(field, geom, 4, _t(pix), N, a, ws)
+    ref = oracle.render(flat.astype(np.float64), cfg, oracle_geom(GEOM), 4, pix, N, mask)
+    np.testing.assert_allclose(_np(a), ref, rtol=1e-5, atol=1e-6)
+    assert np.all(_np(a)[-5:] == 0.0)          # rays that miss the volume
+
+
+# ------------------------------------------------------------------------------ backward
+@pytest.mark.parametrize("case", range(len(FWD_CASES)))
+@pytest.mark.parametrize("loss", [S.LOSS_MSE, S.LOSS_L1])
+def test_train_step_loss_and_gradients_match_oracle(lib, case, loss):
+    cfg = field_cfg(**FWD_CASES[case], loss=loss)
+    flat = S.init_params(cfg, 20 + case, table_scale=0.5).astype(np.float32)
+    N = 53
+    geom = lib.Geometry.from_config(GEOM)
+    og = oracle_geom(GEOM)
+    pix = batch(GEOM, 1, 257, seed=case + 7, n_miss=3)
+    a_meas = np.random.default_rng(case).uniform(0, 0.8, size=len(pix)).astype(np.float32)
+    A, cache = oracle.render_forward(flat.astype(np.float64), cfg, og, 1, pix, N)
+    ref_loss, dLdA = oracle.loss_and_grad(A, a_meas, loss)
+    ref_grad = oracle.render_backward(cache, dLdA, cfg)
+
+    field = lib.Field(cfg, params=flat)
+    ws = lib.workspace(lib.step_workspace_bytes(field, len(pix), N))
+    # gradient through render_backward with the oracle's dL/dA
+    lib.render_backward(field, geom, 1, _t(pix), N, _t(dLdA.astype(np.float32)), ws)
+    g = _np(field.flat_grads())
+    _grad_close(g, ref_grad, cfg, what="render_backward")
+    field.grads.zero_()
+    # the full step: loss, then Adam applied (grads zeroed afterwards)
+    loss_t = torch.zeros(1, device="cuda")
+    lib.train_step(field, geom, 1, _t(pix), _t(a_meas), N, loss_t, ws)
+    assert abs(_np(loss_t)[0] - ref_loss) <= 1e-5 * abs(ref_loss)
+    assert float(field.grads.abs().max()) == 0.0
+    flags, scale, step = field.poll_status()
+    assert step == 1 and flags == 0
+
+
+def test_autograd_function_matches_oracle(lib):
+    cfg = field_cfg(n_levels=16, hidden_layers=4, log2_T=10, max_res=300)
+    flat = S.init_params(cfg, 3, table_scale=0.5).astype(np.float32)
+    field = lib.Field(cfg, params=flat)
+    geom = lib.Geometry.from_config(GEOM)
+    pix = batch(GEOM, 2, 128, seed=9)
+    p = field.flat_params().clone().requires_grad_(True)
+    a = lib.Render.apply(p, field, geom, 2, _t(pix), 40)
+    a_meas = _t(np.full(len(pix), 0.3, dtype=np.float32))
+    loss = ((a - a_meas) ** 2).mean()
+    loss.backward()
+    A, cache = oracle.render_forward(flat.astype(np.float64), cfg, oracle_geom(GEOM), 2, pix, 40)
+    _, dLdA = oracle.loss_and_grad(A, np.full(len(pix), 0.3), S.LOSS_MSE)
+    _grad_close(_np(p.grad), oracle.render_backward(cache, dLdA, cfg), cfg, what="autograd")
+
+
+def test_adam_matches_oracle(lib):
+    cfg = field_cfg(n_levels=8, log2_T=8)
+    flat = S.init_params(cfg, 4).astype(np.float32)
+    field = lib.Field(cfg, params=flat)
+    rng = np.random.default_rng(0)
+    st = oracle.AdamState.zeros(flat.size)
+    p_ref = flat.astype(np.float64)
+    for k in range(3):
+        g = (rng.normal(size=flat.size) * rng.choice([0, 1e-6, 1e-2, 1], size=flat.size)).astype(np.float32)
+        field.grads[: flat.size].copy_(_t(g))
+        lib.optimizer_step(field)
+        p_ref, st, _ = oracle.adam_step(p_ref, g.astype(np.float64), st, cfg)
+        np.testing.assert_allclose(_np(field.flat_params()), p_ref, rtol=2e-6, atol=2e-8)
+        assert float(field.grads.abs().max()) == 0.0
+
+
+def test_training_curve_tracks_oracle(lib):
+    cfg = field_cfg(n_levels=8, hidden_layers=2, log2_T=12, norm=S.NORM_LN_PER_LEVEL)
+    flat = S.init_params(cfg, 5).astype(np.float32)
+    field = lib.Field(cfg, params=flat)
+    geom = lib.Geometry.from_config(GEOM)
+    og = oracle_geom(GEOM)
+    vol, _ = S.phantom(S.WORKLOADS["tiny_fp32"], seed=0, D=24)
+    proj = oracle.project(og, vol, oversample=1)
+    rng = np.random.default_rng(11)
+    st = oracle.AdamState.zeros(flat.size)
+    p_ref = flat.astype(np.float64)
+    N = 32
+    loss_t = torch.zeros(1, device="cuda")
+    for step in range(6):
+        view = int(rng.integers(0, GEOM.n_views))
+        pix = rng.choice(hit_pixels(GEOM, view), size=200, replace=False).astype(np.int32)
+        a_meas = proj[view].ravel()[pix].astype(np.float32)
+        ws = lib.workspace(lib.step_workspace_bytes(field, len(pix), N))
+        lib.train_step(field, geom, view, _t(pix), _t(a_meas), N, loss_t, ws)
+        p_ref, st, ref_loss, _ = oracle.train_step(p_ref, st, cfg, og, view, pix, a_meas, N)
+        assert abs(_np(loss_t)[0] - ref_loss) <= 1e-3 * ref_loss, (step, _np(loss_t)[0], ref_loss)
+
+
+# ------------------------------------------------------------------------------ points / MCI
+@pytest.mark.parametrize("norm", [S.NORM_LN, S.NORM_NONE])
+def test_voxel_loss_gradients_match_oracle(lib, norm):
+    cfg = field_cfg(n_levels=16, hidden_layers=4, log2_T=12, max_res=256, norm=norm)
+    flat = S.init_params(cfg, 6, table_scale=0.5).astype(np.float32)
+    field = lib.Field(cfg, params=flat)
+    rng = np.random.default_rng(2)
+    xyz = rng.random((1000, 3)).astype(np.float32)
+    mu_gt = rng.random(1000).astype(np.float32)
+    ws = lib.workspace(lib.points_workspace_bytes(field, len(xyz)))
+    loss_t = torch.zeros(1, device="cuda")
+    lib.fit_points_backward(field, _t(xyz), _t(mu_gt), loss_t, ws)
+    st = oracle.AdamState.zeros(flat.size)
+    _, _, ref_loss, ref_grad = oracle.fit_points_step(flat.astype(np.float64), st, cfg, xyz, mu_gt, adam=False)
+    assert abs(_np(loss_t)[0] - ref_loss) <= 1e-5 * ref_loss
+    _grad_close(_np(field.flat_grads()), ref_grad, cfg, what="voxel loss")
+
+
+def test_query_volume_and_points_match_oracle(lib):
+    cfg = field_cfg(n_levels=16, hidden_layers=4, log2_T=12, max_res=256)
+    flat = S.init_params(cfg, 7, table_scale=0.5).astype(np.float32)
+    field = lib.Field(cfg, params=flat)
+    D = 13
+    out = torch.empty(D ** 3, device="cuda")
+    lib.query_volume(field, D, out)
+    ref = oracle.query_volume(flat.astype(np.float64), cfg, D)
+    np.testing.assert_allclose(_np(out).reshape(D, D, D), ref, rtol=0, atol=1e-5)
+    xyz = np.random.default_rng(1).random((777, 3)).astype(np.float32)
+    mu = torch.empty(777, device="cuda")
+    lib.query_points(field, _t(xyz), mu)
+    np.testing.assert_allclose(_np(mu), oracle.query_points(flat.astype(np.float64), cfg, xyz), rtol=0, atol=1e-5)
+
+
+def test_projector_matches_oracle(lib):
+    g = S.GeometryConfig(n_views=3, det_nu=24, det_nv=20)
+    geom = lib.Geometry.from_config(g)
+    vol, _ = S.phantom(S.WORKLOADS["tiny_fp32"], seed=3, D=20)
+    out = torch.empty(3 * 20 * 24, device="cuda")
+    lib.project(geom, _t(vol.astype(np.float32)), 2, out)
+    ref = oracle.project(oracle_geom(g), vol.astype(np.float32).astype(np.float64), oversample=2)
+    np.testing.assert_allclose(_np(out).reshape(ref.shape), ref, rtol=1e-5, atol=1e-6)
+
+
+# ------------------------------------------------------------------------------ edge cases
+def test_empty_batch_and_all_miss(lib):
+    cfg = field_cfg()
+    flat = S.init_params(cfg, 8).astype(np.float32)
+    field = lib.Field(cfg, params=flat)
+    geom = lib.Geometry.from_config(GEOM)
+    ws = lib.workspace(lib.step_workspace_bytes(field, 0, 16))
+    loss_t = torch.full((1,), 7.0, device="cuda")
+    lib.train_step(field, geom, 0, torch.empty(0, dtype=torch.int32, device="cuda"),
+                   torch.empty(0, device="cuda"), 16, loss_t, ws)
+    assert _np(loss_t)[0] == 0.0
+    assert np.array_equal(_np(field.flat_params()), flat)
+    miss = np.setdiff1d(np.arange(GEOM.det_nu * GEOM.det_nv), hit_pixels(GEOM, 0))[:50].astype(np.int32)
+    ws = lib.workspace(lib.step_workspace_bytes(field, len(miss), 16))
+    a = torch.full((len(miss),), 5.0, device="cuda")
+    lib.render_forward(field, geom, 0, _t(miss), 16, a, ws)
+    assert np.all(_np(a) == 0.0)
+
+
+def test_nonfinite_measurement_skips_the_step(lib):
+    cfg = field_cfg()
+    flat = S.init_params(cfg, 9).astype(np.float32)
+    field = lib.Field(cfg, params=flat)
+    geom = lib.Geometry.from_config(GEOM)
+    pix = batch(GEOM, 0, 64, seed=1)
+    a_meas = np.zeros(64, dtype=np.float32)
+    a_meas[5] = np.nan
+    ws = lib.workspace(lib.step_workspace_bytes(field, 64, 16))
+    loss_t = torch.zeros(1, device="cuda")
+    lib.train_step(field, geom, 0, _t(pix), _t(a_meas), 16, loss_t, ws)
+    flags, _, step = field.poll_status()
+    assert flags & lib.FLAG_NONFINITE and flags & lib.FLAG_SKIPPED and step == 0
+    assert np.array_equal(_np(field.flat_params()), flat)
+    a_meas[5] = 0.1
+    lib.train_step(field, geom, 0, _t(pix), _t(a_meas), 16, loss_t, ws)
+    flags, _, step = field.poll_status()
+    assert flags == 0 and step == 1
+
+
+def test_argument_errors_are_reported(lib):
+    cfg = field_cfg()
+    field = lib.Field(cfg, params=S.init_params(cfg, 0))
+    geom = lib.Geometry.from_config(GEOM)
+    pix = _t(batch(GEOM, 0, 8, seed=0))
+    small = lib.workspace(16)
+    with pytest.raises(lib.NHError) as e:
+        lib.render_forward(field, geom, 0, pix, 16, torch.empty(8, device="cuda"), small)
+    assert e.value.status == -3
+    with pytest.raises(lib.NHError) as e:
+        lib.render_forward(field, geom, 99, pix, 16, torch.empty(8, device="cuda"), lib.workspace(1 << 16))
+    assert e.value.status == -1
+    with pytest.raises(lib.NHError) as e:
+        lib.Field(replace(cfg, width=64))
+    assert e.value.status == -6
+
+
+# ------------------------------------------------------------------------------ full sizes
+@pytest.mark.parametrize("wname", ["paper_fp32", "large_bf16"])
+def test_full_size_sampled_rays_match_oracle(lib, wname):
+    """The configuration the benchmark times, checked on sampled rays: the forward of
+    every ray runs, the oracle recomputes 6 of them; the backward of two single rays
+    (one-hot dL/dA) is compared on the dense parameters and the touched table rows."""
+    w = S.WORKLOADS[wname]
+    cfg = replace(w.field, precision=S.PREC_F32) if w.field.precision == S.PREC_F32 else w.field
+    flat = S.init_params(cfg, 1, table_scale=0.5).astype(np.float32)
+    field = lib.Field(cfg, params=flat)
+    geom = lib.Geometry.from_config(w.geometry)
+    og = oracle_geom(w.geometry)
+    rng = np.random.default_rng(0)
+    view = 3
+    pix = rng.choice(hit_pixels(w.geometry, view), size=w.n_rays, replace=False).astype(np.int32)
+    N = w.n_samples
+    ws = lib.workspace(lib.step_workspace_bytes(field, len(pix), N))
+    a = torch.empty(len(pix), device="cuda")
+    lib.render_forward(field, geom, view, _t(pix), N, a, ws)
+    ref_flat = rounded_tables(flat, cfg, cfg.precision).astype(np.float64)
+    pick = rng.choice(len(pix), size=6, replace=False)
+    ref = oracle.render(ref_flat, cfg, og, view, pix[pick], N)
+    np.testing.assert_allclose(_np(a)[pick], ref, rtol=1e-5, atol=1e-6)
+    for r in pick[:2]:
+        field.grads.zero_()
+        dLdA = np.zeros(len(pix), dtype=np.float32)
+        dLdA[r] = 1.0
+        lib.render_backward(field, geom, view, _t(pix), N, _t(dLdA), ws)
+        A, cache = oracle.render_forward(ref_flat, cfg, og, view, pix[r:r + 1], N)
+        g_ref = oracle.render_backward(cache, np.array([1.0]), cfg)
+        _grad_close(_np(field.flat_grads()), g_ref, cfg, what=f"{wname} ray {r}")
