@@ -223,6 +223,13 @@ nh_status query_points(const nh_field* f, int32_t n, const float* xyz_dev, float
 /* mu at the D^3 voxel centres ((k + 1/2) / D), out_dev float[D^3] in [z][y][x] order. */
 nh_status query_volume(const nh_field* f, int32_t D, float* out_dev, void* stream);
 
+/* Mean squared difference of two float arrays, accumulated in double with a fixed
+ * reduction order (deterministic): out_dev[0] = (1/n) sum (a - b)^2. With data in
+ * [0, 1] the reconstruction PSNR of Sec. 3.2 is 10 log10(1 / mse). ws: device
+ * scratch of at least 8192 bytes (8-byte aligned). */
+nh_status volume_mse(const float* a_dev, const float* b_dev, int64_t n, double* out_dev, void* ws,
+                     size_t ws_bytes, void* stream);
+
 /* ------------------------------------------------------------------ data synthesis
  * Forward projection of a voxel volume (the TIGRE projections of Sec. 3.1):
  * for every view and pixel, the clipped ray is cut into

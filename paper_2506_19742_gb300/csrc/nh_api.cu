@@ -575,3 +575,14 @@ extern "C" nh_status encode_points(const nh_field* f, int32_t n, const float* xy
     NH_CUDA(launch_encode_points(f->fa, n, xyz, h, S(stream)), "encode_points");
     return NH_OK;
 }
+
+extern "C" nh_status volume_mse(const float* a, const float* b, int64_t n, double* out_dev, void* ws,
+                                size_t ws_bytes, void* stream) {
+    if (!a || !b || !out_dev || !ws) return fail(NH_ERR_INVALID_ARG, "volume_mse: null argument");
+    if (n < 1) return fail(NH_ERR_INVALID_ARG, "volume_mse: n < 1");
+    if (!aligned(ws, 8) || !aligned(out_dev, 8)) return fail(NH_ERR_ALIGNMENT, "volume_mse: misaligned buffer");
+    if (ws_bytes < mse_workspace_bytes()) return fail(NH_ERR_SIZE_MISMATCH, "volume_mse: workspace needs %zu bytes",
+                                                      mse_workspace_bytes());
+    NH_CUDA(launch_mse(a, b, n, out_dev, ws, S(stream)), "volume_mse");
+    return NH_OK;
+}

@@ -83,5 +83,7 @@ cudaError_t launch_hash_corners(const FieldArgs& fa, int n, const float* xyz, ui
 cudaError_t launch_encode_points(const FieldArgs& fa, int n, const float* xyz, float* h,
                                  cudaStream_t st);
 cudaError_t launch_query_volume(const FieldArgs& fa, int D, float* out, cudaStream_t st);
+size_t      mse_workspace_bytes();
+cudaError_t launch_mse(const float* a, const float* b, int64_t n, double* out, void* ws, cudaStream_t st);
 
 }  // namespace nh

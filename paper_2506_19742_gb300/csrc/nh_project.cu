@@ -63,3 +63,52 @@ cudaError_t launch_project(const ViewArgs& va, int view, const float* vol, int D
 }
 
 }  // namespace nh
+
+namespace nh {
+
+// Sum of squared differences in double: fixed grid of partials, then one block
+// sums them in order (deterministic for a given n).
+constexpr int kMseBlocks = 1024;
+
+__global__ void __launch_bounds__(256) k_sq_diff(const float* __restrict__ a, const float* __restrict__ b,
+                                                 int64_t n, double* __restrict__ part) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double d = (double)a[i] - (double)b[i];
+        s += d * d;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void __launch_bounds__(256) k_sum_parts(const double* __restrict__ part, int np, int64_t n,
+                                                   double* __restrict__ out) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = red[0] / (double)n;
+}
+
+size_t mse_workspace_bytes() { return sizeof(double) * kMseBlocks; }
+
+cudaError_t launch_mse(const float* a, const float* b, int64_t n, double* out, void* ws, cudaStream_t st) {
+    k_sq_diff<<<kMseBlocks, 256, 0, st>>>(a, b, n, (double*)ws);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_sum_parts<<<1, 256, 0, st>>>((const double*)ws, kMseBlocks, n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace nh

@@ -97,6 +97,7 @@ _SIGS = {
     "query_points": (_I, [_P, _I, _P, _P, _P]),
     "query_volume": (_I, [_P, _I, _P, _P]),
     "project": (_I, [_P, _P, _I, _I, _P, _P]),
+    "volume_mse": (_I, [_P, _P, C.c_int64, _P, _P, _SZ, _P]),
     "sample_rays": (_I, [_P, _I, _I, _P, _I, _P, _P, _P]),
     "hash_corners": (_I, [_P, _I, _P, _P, _P, _P]),
     "encode_points": (_I, [_P, _I, _P, _P, _P]),
@@ -358,9 +359,33 @@ def query_volume(field, D, out, stream=None):
 
 
 def project(geom, vol, oversample, proj_out, stream=None):
+    """vol: (D, D, D) or flat D^3 float32 CUDA tensor in [z][y][x] order."""
     vol = _dev(vol, torch.float32, "vol")
-    _check(load().project(geom.handle, _ptr(vol), vol.shape[0], int(oversample), _ptr(proj_out),
+    D = vol.shape[0] if vol.dim() == 3 else int(round(vol.numel() ** (1.0 / 3.0)))
+    if D ** 3 != vol.numel():
+        raise ValueError("project: vol must hold D^3 voxels")
+    _check(load().project(geom.handle, _ptr(vol), D, int(oversample), _ptr(proj_out),
                           _stream(stream)), "project")
+
+
+def volume_mse(a, b, out=None, stream=None):
+    """Device mean squared difference (float64 scalar tensor) of two float32 arrays."""
+    a = _dev(a, torch.float32, "a")
+    b = _dev(b, torch.float32, "b")
+    if a.numel() != b.numel():
+        raise ValueError("volume_mse: size mismatch")
+    out = torch.empty(1, dtype=torch.float64, device=a.device) if out is None else out
+    ws = torch.empty(1024, dtype=torch.float64, device=a.device)
+    _check(load().volume_mse(_ptr(a), _ptr(b), a.numel(), _ptr(out), _ptr(ws), 8192, _stream(stream)),
+           "volume_mse")
+    return out
+
+
+def psnr(vol_pred, vol_gt, data_range=1.0, stream=None):
+    """Reconstruction PSNR (Sec. 3.2) in dB: 10 log10(range^2 / mse), mse from the library."""
+    import math
+    mse = float(volume_mse(vol_pred, vol_gt, stream=stream).item())
+    return float("inf") if mse == 0 else 10.0 * math.log10(data_range * data_range / mse)
 
 
 def sample_rays(geom, view, pix, n_samples, xyz_out, delta_out, stream=None):
