@@ -66,11 +66,27 @@ __device__ __forceinline__ void store_lp<__half>(__half* lp, int64_t i, float4 p
 template <>
 __device__ __forceinline__ void store_lp<float>(float*, int64_t, float4) {}
 
+// The update needs a square root and a reciprocal per parameter; the IEEE-rounded
+// forms are multi-instruction sequences that would make this HBM-bound pass
+// instruction-bound, so it uses the single-instruction PTX approximations (a few
+// ulp of relative error in the step, far below the step's own float32 rounding
+// of p).
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 __device__ __forceinline__ float adam1(float& p, float& m, float& v, float g, float b1, float b2,
                                        float eps, float step_size, float inv_bc2_sqrt) {
     m = fmaf(b1, m, (1.f - b1) * g);
     v = fmaf(b2, v, (1.f - b2) * g * g);
-    p = p - step_size * m / (sqrtf(v) * inv_bc2_sqrt + eps);
+    p = fmaf(-step_size * m, rcp_approx(fmaf(sqrt_approx(v), inv_bc2_sqrt, eps)), p);
     return p;
 }
 

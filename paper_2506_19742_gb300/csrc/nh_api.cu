@@ -165,10 +165,15 @@ static nh_status compute_layout(const nh_field_desc* d, nh_field_sizes* s, Field
     s->off_mlp = s->off_beta + D;
     uint64_t mlp = W * D + W + (H - 1) * (W * W + W) + W + 1;
     s->n_params = s->off_mlp + mlp;
-    {   // shared memory of the backward kernels: dense params + mask + grads + 4 warps of scratch
+    {   // backward kernels: 8 warps keep 32 H TMEM columns per thread (two lane-quarter
+        // groups, at most 512 columns), and shared memory holds dense params, mask,
+        // gradient accumulators and 8 warps of transpose scratch
+        if (2 * 32 * H > 512)
+            return fail(NH_ERR_UNSUPPORTED, "field: hidden_layers = %d exceeds the 8 that tensor memory holds",
+                        d->hidden_layers);
         const uint64_t nd4 = align_up(s->n_params - s->n_table_params, 4);
-        const uint64_t scratch = 32 * (D + 1) + H * 32 * (W + 1) + 32 * W;
-        const uint64_t bytes = 4 * (2 * nd4 + kMaxD + 4 * scratch);
+        const uint64_t scratch = 32 * (W + 1) + 32 * W;
+        const uint64_t bytes = 4 * (2 * nd4 + kMaxD + 8 * scratch);
         if (bytes > 227 * 1024)
             return fail(NH_ERR_UNSUPPORTED, "field: hidden_layers = %d needs %llu bytes of shared memory",
                         d->hidden_layers, (unsigned long long)bytes);

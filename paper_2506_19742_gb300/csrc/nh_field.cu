@@ -1,679 +1,95 @@
-// Field kernels of the NeRF-CBCT training step (float32 FFMA MLP).
-//
-//  k_ray_forward   one warp per (ray, 32-sample chunk): sample -> hash gather ->
-//                  Normalized Hash Encoder -> MLP -> mu; the warp's partial of the
-//                  Beer-Lambert sum A = sum_i mu_i delta_i (Eq. 1) goes to ray_part.
-//  k_ray_loss      ray sums in fixed chunk order, MSE / L1 loss (Eq. 3) and dL/dA.
-//  k_ray_backward  recomputes the forward of each sample (features are never
-//                  stored in HBM), then MLP backward, LN backward and the hash
-//                  scatter-add (red.global.add.v2.f32); MLP / LN weight gradients
-//                  are reduced per warp and per CTA in shared memory and flushed
-//                  once per CTA.
-//  k_points        the same field at explicit points: query (forward) or the MCI
-//                  voxel-loss step (Eq. 2, forward + backward in one pass).
-#include <cuda_runtime.h>
-
-#include "nh_device.cuh"
-#include "nh_internal.h"
+// Precision-independent launchers of the field kernels and the public dispatch on
+// the table precision (the templated launchers live in nh_field_{f32,bf16,f16}.cu).
+#include "nh_field.cuh"
 
 namespace nh {
 
-constexpr int kW = 32;   // MLP width compiled in
-
-// Offsets inside the dense parameter block (gamma at 0, beta at D, then W_k, b_k).
-struct DenseLayout {
-    int D, H;
-    __device__ __forceinline__ int W(int k) const {   // start of W_k
-        // W_0: [kW][D]; W_1..W_{H-1}: [kW][kW]; W_H: [1][kW]
-        if (k == 0) return 2 * D;
-        return 2 * D + (kW * D + kW) + (k - 1) * (kW * kW + kW);
-    }
-    __device__ __forceinline__ int b(int k) const {
-        if (k == 0) return 2 * D + kW * D;
-        if (k < H) return W(k) + kW * kW;
-        return W(k) + kW;
-    }
-};
-
-__device__ __forceinline__ void load_dense(const FieldArgs& fa, float* sp, float* smask) {
-    const float* src = fa.params + fa.n_table;
-    for (int k = threadIdx.x; k < fa.n_dense; k += blockDim.x) sp[k] = src[k];
-    for (int k = threadIdx.x; k < fa.D; k += blockDim.x) smask[k] = fa.state->mask[k];
-}
-
-template <typename TT>
-__device__ __forceinline__ const void* table_base(const FieldArgs& fa) {
-    return sizeof(TT) == 4 ? (const void*)fa.params : fa.tables_lp;
-}
-
-// Normalized Hash Encoder forward: hhat (or h when norm = none), per-group rstd, y.
-template <int D>
-__device__ __forceinline__ void nhe_forward(const FieldArgs& fa, const float* sp, const float* smask,
-                                            const float (&h)[D], float (&hhat)[D],
-                                            float (&rstd)[D / 2], float (&y)[D]) {
-    if (fa.norm == NH_NORM_LN) {
-        float r1[1];
-        ln_stats<D, D>(h, fa.eps, hhat, r1);
-#pragma unroll
-        for (int g = 0; g < D / 2; g++) rstd[g] = r1[0];
-    } else if (fa.norm == NH_NORM_LN_PER_LEVEL) {
-        ln_stats<D, 2>(h, fa.eps, hhat, rstd);
-    } else {
-#pragma unroll
-        for (int k = 0; k < D; k++) hhat[k] = h[k];
-#pragma unroll
-        for (int g = 0; g < D / 2; g++) rstd[g] = 1.f;
-    }
-    const bool affine = fa.norm != NH_NORM_NONE;
-#pragma unroll
-    for (int k = 0; k < D; k++) {
-        const float gk = affine ? sp[k] : 1.f;
-        const float bk = affine ? sp[D + k] : 0.f;
-        y[k] = fmaf(gk, hhat[k], bk) * smask[k];
-    }
-}
-
-// mu = sigmoid(MLP(y)) without storing activations.
-template <int D>
-__device__ __forceinline__ float mlp_mu(const DenseLayout& lay, const float* sp, const float (&y)[D]) {
-    float a[kW], z[kW];
-    linear_fwd<D, kW>(sp + lay.W(0), sp + lay.b(0), y, z);
-#pragma unroll
-    for (int j = 0; j < kW; j++) a[j] = fmaxf(z[j], 0.f);
-#pragma unroll 1
-    for (int k = 1; k < lay.H; k++) {
-        linear_fwd<kW, kW>(sp + lay.W(k), sp + lay.b(k), a, z);
-#pragma unroll
-        for (int j = 0; j < kW; j++) a[j] = fmaxf(z[j], 0.f);
-    }
-    const float* wo = sp + lay.W(lay.H);
-    float zo = sp[lay.b(lay.H)];
-#pragma unroll
-    for (int j = 0; j < kW; j++) zo = fmaf(wo[j], a[j], zo);
-    return 1.f / (1.f + expf(-zo));
-}
-
-template <int D, typename TT>
-__device__ __forceinline__ float field_mu(const FieldArgs& fa, const float* sp, const float* smask,
-                                          const float x[3]) {
-    float h[D], hhat[D], rstd[D / 2], y[D];
-    encode_point<D / 2, TT>(fa, table_base<TT>(fa), x, h);
-    nhe_forward<D>(fa, sp, smask, h, hhat, rstd, y);
-    const DenseLayout lay{D, fa.H};
-    return mlp_mu<D>(lay, sp, y);
-}
-
-// ============================================================================ forward
-template <int D, typename TT>
-__global__ void __launch_bounds__(256) k_ray_forward(FieldArgs fa, ViewArgs va,
-                                                     const int32_t* __restrict__ pix, int R, int N,
-                                                     int C, float* __restrict__ ray_part) {
-    extern __shared__ __align__(16) float smem[];
-    float* sp = smem;
-    float* smask = smem + ((fa.n_dense + 3) & ~3);
-    load_dense(fa, sp, smask);
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long task = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
-    if (task >= (long long)R * C) return;
-    const int r = (int)(task / C), c = (int)(task - (long long)r * C);
-    const RayGeo g = ray_setup(va, pix[r], N);
-    if (!g.hit) {
-        if (lane == 0) ray_part[task] = 0.f;
-        return;
-    }
-    const int i = c * 32 + lane;
-    float mu = 0.f;
-    if (i < N) {
-        float x[3];
-        sample_position(g, i, x);
-        mu = field_mu<D, TT>(fa, sp, smask, x);
-    }
-    const float s = warp_sum(mu);
-    if (lane == 0) ray_part[task] = s * g.delta;
-}
-
-// ============================================================================ loss
-// One CTA: A_r = sum over chunks in order, loss = mean over rays, dL/dA_r.
-__global__ void __launch_bounds__(1024) k_ray_loss(const float* __restrict__ ray_part, int R, int C,
-                                                   const float* __restrict__ a_meas, int loss_kind,
-                                                   float* __restrict__ a_pred, float* __restrict__ dLdA,
-                                                   float* __restrict__ loss_out, DeviceState* state) {
-    __shared__ float red[32];
-    float acc = 0.f;
-    const float invR = 1.f / (float)R;
-    for (int r = threadIdx.x; r < R; r += blockDim.x) {
-        float A = 0.f;
-        for (int c = 0; c < C; c++) A += ray_part[(size_t)r * C + c];
-        if (a_pred) a_pred[r] = A;
-        if (a_meas) {
-            const float res = A - a_meas[r];
-            float l, gr;
-            if (loss_kind == NH_LOSS_MSE) {
-                l = res * res;
-                gr = 2.f * res * invR;
-            } else {
-                l = fabsf(res);
-                gr = (res > 0.f ? 1.f : (res < 0.f ? -1.f : 0.f)) * invR;
-            }
-            acc += l;
-            if (dLdA) dLdA[r] = gr;
-        }
-    }
-    acc = warp_sum(acc);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        float v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
-        v = warp_sum(v);
-        if (threadIdx.x == 0 && a_meas) {
-            const float loss = v * invR;
-            if (loss_out) *loss_out = loss;
-            if (!isfinite(loss)) atomicOr(&state->flags, NH_FLAG_NONFINITE);
-        }
-    }
-}
-
-// ============================================================================ backward
-// Per-warp shared scratch (floats): act0 [32][D+1] (hhat rows), act_k [H][32][kW+1]
-// (hidden activations after ReLU), dz [32][kW] (XOR-swizzled float4 groups).
-__host__ __device__ constexpr int warp_scratch_floats(int D, int H) {
-    return 32 * (D + 1) + H * 32 * (kW + 1) + 32 * kW;
-}
-
-__device__ __forceinline__ int swz(int s, int j) {   // column j of dz row s
-    return s * kW + ((((j >> 2) ^ (s & 7)) << 2) | (j & 3));
-}
-
-// Stores this lane's dz row, then the warp reduces dW[j][i] = sum_s dz[s][j] in[s][i]
-// (lane i; in[s][i] = ga_i * act[s][i] + be_i) and db[j] = sum_s dz[s][j] (lane j)
-// into the CTA accumulators.
-template <int IN>
-__device__ __forceinline__ void warp_weight_grad(float* dzb, const float* act, int act_stride,
-                                                 const float (&dz)[kW], float ga, float be,
-                                                 float* sgW, float* sgb, int lane) {
-#pragma unroll
-    for (int q = 0; q < kW / 4; q++)
-        *reinterpret_cast<float4*>(dzb + lane * kW + (((q ^ (lane & 7))) << 2)) =
-            make_float4(dz[4 * q], dz[4 * q + 1], dz[4 * q + 2], dz[4 * q + 3]);
-    __syncwarp();
-    if (lane < IN) {
-        float acc[kW];
-#pragma unroll
-        for (int j = 0; j < kW; j++) acc[j] = 0.f;
-#pragma unroll 4
-        for (int s = 0; s < 32; s++) {
-            const float a = fmaf(ga, act[s * act_stride + lane], be);
-#pragma unroll
-            for (int q = 0; q < kW / 4; q++) {
-                const float4 d = *reinterpret_cast<const float4*>(dzb + s * kW + ((q ^ (s & 7)) << 2));
-                acc[4 * q] = fmaf(d.x, a, acc[4 * q]);
-                acc[4 * q + 1] = fmaf(d.y, a, acc[4 * q + 1]);
-                acc[4 * q + 2] = fmaf(d.z, a, acc[4 * q + 2]);
-                acc[4 * q + 3] = fmaf(d.w, a, acc[4 * q + 3]);
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < kW; j++) atomicAdd(sgW + j * IN + lane, acc[j]);
-    }
-    float bsum = 0.f;
-#pragma unroll 8
-    for (int s = 0; s < 32; s++) bsum += dzb[swz(s, lane)];
-    atomicAdd(sgb + lane, bsum);
-    __syncwarp();
-}
-
-// Forward with stored activations, then the full backward of one sample per lane.
-// dmu_of(mu) gives dL/dmu (already multiplied by the loss scale); inactive lanes
-// pass dmu = 0 and skip the scatter. Returns mu.
-template <int D, typename TT, class DmuFn>
-__device__ __forceinline__ float sample_fwd_bwd(const FieldArgs& fa, const float* sp, const float* smask,
-                                                float* sg, float* wbuf, const float x[3], bool active,
-                                                int lane, DmuFn dmu_of) {
-    constexpr int L = D / 2;
-    constexpr int SD = D + 1, SW = kW + 1;
-    const DenseLayout lay{D, fa.H};
-    const int H = fa.H;
-    float* act0 = wbuf;
-    float* actk = wbuf + 32 * SD;                    // layer k >= 1 at actk + (k-1)*32*SW
-    float* dzb = actk + H * 32 * SW;
-
-    float hhat[D], rstd[D / 2];
-    float a[kW];
-    {
-        float h[D], y[D];
-        encode_point<L, TT>(fa, table_base<TT>(fa), x, h);
-        nhe_forward<D>(fa, sp, smask, h, hhat, rstd, y);
-#pragma unroll
-        for (int k = 0; k < D; k++) act0[lane * SD + k] = hhat[k];
-        float z[kW];
-        linear_fwd<D, kW>(sp + lay.W(0), sp + lay.b(0), y, z);
-#pragma unroll
-        for (int j = 0; j < kW; j++) {
-            a[j] = fmaxf(z[j], 0.f);
-            actk[lane * SW + j] = a[j];
-        }
-    }
-#pragma unroll 1
-    for (int k = 1; k < H; k++) {
-        float z[kW];
-        linear_fwd<kW, kW>(sp + lay.W(k), sp + lay.b(k), a, z);
-        float* dst = actk + k * 32 * SW + lane * SW;
-#pragma unroll
-        for (int j = 0; j < kW; j++) {
-            a[j] = fmaxf(z[j], 0.f);
-            dst[j] = a[j];
-        }
-    }
-    const float* wo = sp + lay.W(H);
-    float zo = sp[lay.b(H)];
-#pragma unroll
-    for (int j = 0; j < kW; j++) zo = fmaf(wo[j], a[j], zo);
-    const float mu = 1.f / (1.f + expf(-zo));
-    const float dmu = active ? dmu_of(mu) : 0.f;
-    const float dzo = dmu * mu * (1.f - mu);
-
-    // output layer: dW_H[0][i] = sum_s dzo[s] a_H[s][i], db_H = sum_s dzo[s]
-    {
-        const float* aH = actk + (H - 1) * 32 * SW;
-        dzb[lane] = dzo;
-        __syncwarp();
-        float acc = 0.f;
-#pragma unroll 8
-        for (int s = 0; s < 32; s++) acc = fmaf(dzb[s], aH[s * SW + lane], acc);
-        atomicAdd(sg + lay.W(H) + lane, acc);
-        const float bs = warp_sum(dzo);
-        if (lane == 0) atomicAdd(sg + lay.b(H), bs);
-        __syncwarp();
-    }
-    float dz[kW];
-#pragma unroll
-    for (int j = 0; j < kW; j++) dz[j] = (a[j] > 0.f) ? wo[j] * dzo : 0.f;
-
-    // hidden layers k = H-1 .. 1: input act_k (ReLU output of layer k-1)
-#pragma unroll 1
-    for (int k = H - 1; k >= 1; k--) {
-        const float* ak = actk + (k - 1) * 32 * SW;
-        warp_weight_grad<kW>(dzb, ak, SW, dz, 1.f, 0.f, sg + lay.W(k), sg + lay.b(k), lane);
-        float din[kW];
-        linear_bwd_data<kW, kW>(sp + lay.W(k), dz, din);
-#pragma unroll
-        for (int i = 0; i < kW; i++) dz[i] = (ak[lane * SW + i] > 0.f) ? din[i] : 0.f;
-    }
-
-    // layer 0: input y = (gamma hhat + beta) m
-    const bool affine = fa.norm != NH_NORM_NONE;
-    {
-        const int il = lane < D ? lane : 0;
-        const float ga = (affine ? sp[il] : 1.f) * smask[il];
-        const float be = affine ? sp[D + il] * smask[il] : 0.f;
-        warp_weight_grad<D>(dzb, act0, SD, dz, ga, be, sg + lay.W(0), sg + lay.b(0), lane);
-    }
-    float dh[D];
-    linear_bwd_data<D, kW>(sp + lay.W(0), dz, dh);   // dh <- dL/dy
-#pragma unroll
-    for (int k = 0; k < D; k++) dh[k] *= smask[k];     // dL/d(gamma hhat + beta)
-
-    if (affine) {
-        // dgamma_k = sum_s dy'_k hhat_k, dbeta_k = sum_s dy'_k, transposed through dzb:
-        // lane s stores element k of its row at column k ^ s (conflict-free both ways).
-        float* col = dzb;
-#pragma unroll
-        for (int k = 0; k < D; k++) col[lane * kW + (k ^ lane)] = dh[k] * hhat[k];
-        __syncwarp();
-        if (lane < D) {
-            float s = 0.f;
-#pragma unroll 8
-            for (int t = 0; t < 32; t++) s += col[t * kW + (lane ^ t)];
-            atomicAdd(sg + lane, s);
-        }
-        __syncwarp();
-#pragma unroll
-        for (int k = 0; k < D; k++) col[lane * kW + (k ^ lane)] = dh[k];
-        __syncwarp();
-        if (lane < D) {
-            float s = 0.f;
-#pragma unroll 8
-            for (int t = 0; t < 32; t++) s += col[t * kW + (lane ^ t)];
-            atomicAdd(sg + D + lane, s);
-        }
-        __syncwarp();
-#pragma unroll
-        for (int k = 0; k < D; k++) dh[k] *= sp[k];   // dL/dhhat
-        if (fa.norm == NH_NORM_LN) {
-            float r1[1] = {rstd[0]};
-            ln_backward<D, D>(hhat, r1, dh);
-        } else {
-            ln_backward<D, 2>(hhat, rstd, dh);
-        }
-    }
-    bool bad = false;
-#pragma unroll
-    for (int k = 0; k < D; k++) bad |= !isfinite(dh[k]);
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&fa.state->flags, NH_FLAG_NONFINITE);
-    if (active) scatter_point<L>(fa, x, dh);
-    return mu;
-}
-
-template <int D, typename TT>
-__global__ void __launch_bounds__(128) k_ray_backward(FieldArgs fa, ViewArgs va,
-                                                      const int32_t* __restrict__ pix, int R, int N,
-                                                      int C, const float* __restrict__ dLdA) {
-    extern __shared__ __align__(16) float smem[];
-    const int ndp = (fa.n_dense + 3) & ~3;
-    float* sp = smem;
-    float* smask = sp + ndp;
-    float* sg = smask + kMaxD;
-    float* wbase = sg + ndp;
-    load_dense(fa, sp, smask);
-    for (int k = threadIdx.x; k < ndp; k += blockDim.x) sg[k] = 0.f;
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nwarps = blockDim.x >> 5;
-    float* wbuf = wbase + warp * warp_scratch_floats(D, fa.H);
-    const float scale = fa.state->loss_scale;
-    const long long ntask = (long long)R * C;
-    for (long long task = (long long)blockIdx.x * nwarps + warp; task < ntask;
-         task += (long long)gridDim.x * nwarps) {
-        const int r = (int)(task / C), c = (int)(task - (long long)r * C);
-        const RayGeo g = ray_setup(va, pix[r], N);
-        if (!g.hit) continue;
-        const int i = c * 32 + lane;
-        const bool active = i < N;
-        float x[3];
-        sample_position(g, active ? i : N - 1, x);
-        const float gr = dLdA[r] * g.delta * scale;
-        sample_fwd_bwd<D, TT>(fa, sp, smask, sg, wbuf, x, active, lane, [gr](float) { return gr; });
-    }
-    __syncthreads();
-    float* gd = fa.grads + fa.n_table;
-    for (int k = threadIdx.x; k < fa.n_dense; k += blockDim.x) {
-        const float v = sg[k];
-        if (v != 0.f) atomicAdd(gd + k, v);
-    }
-}
-
-// ============================================================================ points
-// query (mu_gt == null): mu_out[p] = M(x_p). fit: forward + backward of the voxel
-// L1 loss (Eq. 2), one CTA partial of sum |mu - mu_gt| per block.
-template <int D, typename TT>
-__global__ void __launch_bounds__(128) k_points(FieldArgs fa, int n, const float* __restrict__ xyz,
-                                                const float* __restrict__ mu_gt,
-                                                float* __restrict__ mu_out,
-                                                float* __restrict__ loss_part) {
-    extern __shared__ __align__(16) float smem[];
-    const int ndp = (fa.n_dense + 3) & ~3;
-    float* sp = smem;
-    float* smask = sp + ndp;
-    float* sg = smask + kMaxD;
-    float* wbase = sg + ndp;
-    load_dense(fa, sp, smask);
-    const bool fit = mu_gt != nullptr;
-    if (fit)
-        for (int k = threadIdx.x; k < ndp; k += blockDim.x) sg[k] = 0.f;
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nwarps = blockDim.x >> 5;
-    float lsum = 0.f;
-    if (!fit) {
-        for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
-             p += (long long)gridDim.x * blockDim.x) {
-            const float x[3] = {xyz[3 * p], xyz[3 * p + 1], xyz[3 * p + 2]};
-            mu_out[p] = field_mu<D, TT>(fa, sp, smask, x);
-        }
-        return;
-    }
-    float* wbuf = wbase + warp * warp_scratch_floats(D, fa.H);
-    const float scale = fa.state->loss_scale / (float)n;
-    const long long ntask = ((long long)n + 31) / 32;
-    for (long long task = (long long)blockIdx.x * nwarps + warp; task < ntask;
-         task += (long long)gridDim.x * nwarps) {
-        const long long p = task * 32 + lane;
-        const bool active = p < n;
-        const long long pc = active ? p : (long long)n - 1;
-        const float x[3] = {xyz[3 * pc], xyz[3 * pc + 1], xyz[3 * pc + 2]};
-        const float gt = mu_gt[pc];
-        const float mu = sample_fwd_bwd<D, TT>(fa, sp, smask, sg, wbuf, x, active, lane,
-                                               [gt, scale](float m) {
-                                                   const float r = m - gt;
-                                                   return (r > 0.f ? scale : (r < 0.f ? -scale : 0.f));
-                                               });
-        if (active) {
-            if (mu_out) mu_out[p] = mu;
-            lsum += fabsf(mu - gt);
-        }
-    }
-    __syncthreads();
-    float* gd = fa.grads + fa.n_table;
-    for (int k = threadIdx.x; k < fa.n_dense; k += blockDim.x) {
-        const float v = sg[k];
-        if (v != 0.f) atomicAdd(gd + k, v);
-    }
-    // deterministic CTA partial of the loss
-    __shared__ float red[32];
-    lsum = warp_sum(lsum);
-    if (lane == 0) red[warp] = lsum;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float s = 0.f;
-        for (int w = 0; w < nwarps; w++) s += red[w];
-        loss_part[blockIdx.x] = s;
-    }
-}
-
-__global__ void k_points_loss(const float* __restrict__ part, int n_part, int n, float* loss_out,
-                              DeviceState* state) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    float s = 0.f;
-    for (int k = 0; k < n_part; k++) s += part[k];
-    const float loss = s / (float)n;
-    if (loss_out) *loss_out = loss;
-    if (!isfinite(loss)) atomicOr(&state->flags, NH_FLAG_NONFINITE);
-}
-
-// ============================================================================ probes
-__global__ void k_sample_rays(ViewArgs va, const int32_t* __restrict__ pix, int R, int N,
-                              float* __restrict__ xyz, float* __restrict__ delta) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long long)R * N) return;
-    const int r = (int)(t / N), i = (int)(t - (long long)r * N);
-    const RayGeo g = ray_setup(va, pix[r], N);
-    float x[3];
-    sample_position(g, i, x);
-    xyz[3 * t] = x[0];
-    xyz[3 * t + 1] = x[1];
-    xyz[3 * t + 2] = x[2];
-    if (i == 0) delta[r] = g.delta;
-}
-
-__global__ void k_hash_corners(FieldArgs fa, int n, const float* __restrict__ xyz,
-                               uint32_t* __restrict__ idx, float* __restrict__ wout) {
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    const float x[3] = {xyz[3 * p], xyz[3 * p + 1], xyz[3 * p + 2]};
-    for (int l = 0; l < fa.L; l++) {
-        uint32_t c[3];
-        float w[3];
-        level_cell(x, fa.res[l], c, w);
-        const bool dense = (fa.dense_mask >> l) & 1u;
-        for (int k = 0; k < 8; k++) {
-            uint32_t id;
-            float wk;
-            corner(c, w, k, (uint32_t)fa.res[l] + 1u, dense, fa.Tmask, id, wk);
-            idx[(p * fa.L + l) * 8 + k] = id;
-            wout[(p * fa.L + l) * 8 + k] = wk;
-        }
-    }
-}
-
-template <int D, typename TT>
-__global__ void k_encode_points(FieldArgs fa, int n, const float* __restrict__ xyz, float* __restrict__ hout) {
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    const float x[3] = {xyz[3 * p], xyz[3 * p + 1], xyz[3 * p + 2]};
-    float h[D];
-    encode_point<D / 2, TT>(fa, table_base<TT>(fa), x, h);
-#pragma unroll
-    for (int k = 0; k < D; k++) hout[p * D + k] = h[k];
-}
-
-__global__ void k_voxel_centres(int D, float* __restrict__ xyz) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long n = (long long)D * D * D;
-    if (t >= n) return;
-    const int x = (int)(t % D), y = (int)((t / D) % D), z = (int)(t / ((long long)D * D));
-    const float fD = (float)D;
-    xyz[3 * t] = __fdiv_rn(__fadd_rn((float)x, 0.5f), fD);
-    xyz[3 * t + 1] = __fdiv_rn(__fadd_rn((float)y, 0.5f), fD);
-    xyz[3 * t + 2] = __fdiv_rn(__fadd_rn((float)z, 0.5f), fD);
-}
-
-// Query at voxel centres without materialising the coordinates.
-template <int D_, typename TT>
-__global__ void __launch_bounds__(256) k_query_volume(FieldArgs fa, int D, float* __restrict__ out) {
-    extern __shared__ __align__(16) float smem[];
-    float* sp = smem;
-    float* smask = smem + ((fa.n_dense + 3) & ~3);
-    load_dense(fa, sp, smask);
-    __syncthreads();
-    const long long n = (long long)D * D * D;
-    const float fD = (float)D;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
-         t += (long long)gridDim.x * blockDim.x) {
-        const int xi = (int)(t % D), yi = (int)((t / D) % D), zi = (int)(t / ((long long)D * D));
-        const float x[3] = {__fdiv_rn(__fadd_rn((float)xi, 0.5f), fD),
-                            __fdiv_rn(__fadd_rn((float)yi, 0.5f), fD),
-                            __fdiv_rn(__fadd_rn((float)zi, 0.5f), fD)};
-        out[t] = field_mu<D_, TT>(fa, sp, smask, x);
-    }
-}
-
-// ============================================================================ launchers
-static int g_num_sms = 0;
-static int num_sms() {
-    if (g_num_sms == 0) {
+int num_sms() {
+    static int n = 0;
+    if (n == 0) {
         int dev = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-        if (g_num_sms <= 0) g_num_sms = 1;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
     }
-    return g_num_sms;
+    return n;
 }
 
-static size_t dense_smem(const FieldArgs& fa) {
-    return (size_t)(((fa.n_dense + 3) & ~3) + kMaxD) * sizeof(float);
-}
-static size_t bwd_smem(const FieldArgs& fa, int warps) {
-    return dense_smem(fa) + (size_t)((fa.n_dense + 3) & ~3) * sizeof(float) +
-           (size_t)warps * warp_scratch_floats(fa.D, fa.H) * sizeof(float);
+extern template cudaError_t launch_ray_forward_tt<float>(const FieldArgs&, const ViewArgs&, const int32_t*, int, int, float*, cudaStream_t);
+extern template cudaError_t launch_ray_forward_tt<__nv_bfloat16>(const FieldArgs&, const ViewArgs&, const int32_t*, int, int, float*, cudaStream_t);
+extern template cudaError_t launch_ray_forward_tt<__half>(const FieldArgs&, const ViewArgs&, const int32_t*, int, int, float*, cudaStream_t);
+extern template cudaError_t launch_ray_backward_tt<float>(const FieldArgs&, const ViewArgs&, const int32_t*, int, int, const float*, cudaStream_t);
+extern template cudaError_t launch_ray_backward_tt<__nv_bfloat16>(const FieldArgs&, const ViewArgs&, const int32_t*, int, int, const float*, cudaStream_t);
+extern template cudaError_t launch_ray_backward_tt<__half>(const FieldArgs&, const ViewArgs&, const int32_t*, int, int, const float*, cudaStream_t);
+extern template cudaError_t launch_points_tt<float>(const FieldArgs&, int, const float*, const float*, float*, float*, int, float*, cudaStream_t);
+extern template cudaError_t launch_points_tt<__nv_bfloat16>(const FieldArgs&, int, const float*, const float*, float*, float*, int, float*, cudaStream_t);
+extern template cudaError_t launch_points_tt<__half>(const FieldArgs&, int, const float*, const float*, float*, float*, int, float*, cudaStream_t);
+extern template cudaError_t launch_encode_points_tt<float>(const FieldArgs&, int, const float*, float*, cudaStream_t);
+extern template cudaError_t launch_encode_points_tt<__nv_bfloat16>(const FieldArgs&, int, const float*, float*, cudaStream_t);
+extern template cudaError_t launch_encode_points_tt<__half>(const FieldArgs&, int, const float*, float*, cudaStream_t);
+extern template cudaError_t launch_query_volume_tt<float>(const FieldArgs&, int, float*, cudaStream_t);
+extern template cudaError_t launch_query_volume_tt<__nv_bfloat16>(const FieldArgs&, int, float*, cudaStream_t);
+extern template cudaError_t launch_query_volume_tt<__half>(const FieldArgs&, int, float*, cudaStream_t);
+
+cudaError_t launch_ray_forward(const FieldArgs& fa, const ViewArgs& va, const int32_t* pix, int R, int N,
+                               float* ray_part, cudaStream_t st) {
+    switch (fa.precision) {
+        case NH_PREC_F32: return launch_ray_forward_tt<float>(fa, va, pix, R, N, ray_part, st);
+        case NH_PREC_BF16: return launch_ray_forward_tt<__nv_bfloat16>(fa, va, pix, R, N, ray_part, st);
+        case NH_PREC_F16: return launch_ray_forward_tt<__half>(fa, va, pix, R, N, ray_part, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
-// Dispatch on (D, table type).
-#define NH_DISPATCH(fa, ...)                                                    \
-    do {                                                                                \
-        if ((fa).D == 16 && (fa).precision == NH_PREC_F32) { constexpr int D_ = 16; using TT = float; __VA_ARGS__; } \
-        else if ((fa).D == 32 && (fa).precision == NH_PREC_F32) { constexpr int D_ = 32; using TT = float; __VA_ARGS__; } \
-        else if ((fa).D == 16 && (fa).precision == NH_PREC_BF16) { constexpr int D_ = 16; using TT = __nv_bfloat16; __VA_ARGS__; } \
-        else if ((fa).D == 32 && (fa).precision == NH_PREC_BF16) { constexpr int D_ = 32; using TT = __nv_bfloat16; __VA_ARGS__; } \
-        else if ((fa).D == 16 && (fa).precision == NH_PREC_F16) { constexpr int D_ = 16; using TT = __half; __VA_ARGS__; } \
-        else if ((fa).D == 32 && (fa).precision == NH_PREC_F16) { constexpr int D_ = 32; using TT = __half; __VA_ARGS__; } \
-        else return cudaErrorInvalidValue;                                              \
-    } while (0)
-
-template <typename K>
-static cudaError_t set_smem(K kernel, size_t bytes) {
-    if (bytes > 48 * 1024)
-        return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    return cudaSuccess;
+cudaError_t launch_ray_backward(const FieldArgs& fa, const ViewArgs& va, const int32_t* pix, int R, int N,
+                                const float* dLdA, cudaStream_t st) {
+    switch (fa.precision) {
+        case NH_PREC_F32: return launch_ray_backward_tt<float>(fa, va, pix, R, N, dLdA, st);
+        case NH_PREC_BF16: return launch_ray_backward_tt<__nv_bfloat16>(fa, va, pix, R, N, dLdA, st);
+        case NH_PREC_F16: return launch_ray_backward_tt<__half>(fa, va, pix, R, N, dLdA, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
-cudaError_t launch_ray_forward(const FieldArgs& fa, const ViewArgs& va, const int32_t* pix, int R,
-                               int N, float* ray_part, cudaStream_t st) {
-    const int C = (N + 31) / 32;
-    const long long tasks = (long long)R * C;
-    if (tasks == 0) return cudaSuccess;
-    const int threads = 256;
-    const long long blocks = (tasks + 7) / 8;
-    const size_t sm = dense_smem(fa);
-    NH_DISPATCH(fa, {
-        auto k = k_ray_forward<D_, TT>;
-        cudaError_t e = set_smem(k, sm);
-        if (e != cudaSuccess) return e;
-        k<<<(unsigned)blocks, threads, sm, st>>>(fa, va, pix, R, N, C, ray_part);
-    });
-    return cudaGetLastError();
+cudaError_t launch_points(const FieldArgs& fa, int n, const float* xyz, const float* mu_gt, float* mu_out,
+                          float* loss_part, int n_part, float* loss_out, cudaStream_t st) {
+    switch (fa.precision) {
+        case NH_PREC_F32: return launch_points_tt<float>(fa, n, xyz, mu_gt, mu_out, loss_part, n_part, loss_out, st);
+        case NH_PREC_BF16: return launch_points_tt<__nv_bfloat16>(fa, n, xyz, mu_gt, mu_out, loss_part, n_part, loss_out, st);
+        case NH_PREC_F16: return launch_points_tt<__half>(fa, n, xyz, mu_gt, mu_out, loss_part, n_part, loss_out, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_encode_points(const FieldArgs& fa, int n, const float* xyz, float* h, cudaStream_t st) {
+    switch (fa.precision) {
+        case NH_PREC_F32: return launch_encode_points_tt<float>(fa, n, xyz, h, st);
+        case NH_PREC_BF16: return launch_encode_points_tt<__nv_bfloat16>(fa, n, xyz, h, st);
+        case NH_PREC_F16: return launch_encode_points_tt<__half>(fa, n, xyz, h, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_query_volume(const FieldArgs& fa, int D, float* out, cudaStream_t st) {
+    switch (fa.precision) {
+        case NH_PREC_F32: return launch_query_volume_tt<float>(fa, D, out, st);
+        case NH_PREC_BF16: return launch_query_volume_tt<__nv_bfloat16>(fa, D, out, st);
+        case NH_PREC_F16: return launch_query_volume_tt<__half>(fa, D, out, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_ray_loss(const float* ray_part, int R, int C, const float* a_meas, int loss_kind,
-                            float* a_pred, float* dLdA, float* loss_out, DeviceState* state,
-                            bool, cudaStream_t st) {
+                            float* a_pred, float* dLdA, float* loss_out, DeviceState* state, bool,
+                            cudaStream_t st) {
     k_ray_loss<<<1, 1024, 0, st>>>(ray_part, R, C, a_meas, loss_kind, a_pred, dLdA, loss_out, state);
     return cudaGetLastError();
 }
 
-static constexpr int kBwdWarps = 4;
+int points_partials(int) { return 4096; }
 
-cudaError_t launch_ray_backward(const FieldArgs& fa, const ViewArgs& va, const int32_t* pix, int R,
-                                int N, const float* dLdA, cudaStream_t st) {
-    const int C = (N + 31) / 32;
-    const long long tasks = (long long)R * C;
-    if (tasks == 0) return cudaSuccess;
-    const size_t sm = bwd_smem(fa, kBwdWarps);
-    NH_DISPATCH(fa, {
-        auto k = k_ray_backward<D_, TT>;
-        cudaError_t e = set_smem(k, sm);
-        if (e != cudaSuccess) return e;
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kBwdWarps * 32, sm);
-        if (per_sm < 1) per_sm = 1;
-        long long blocks = (long long)num_sms() * per_sm;
-        const long long need = (tasks + kBwdWarps - 1) / kBwdWarps;
-        if (blocks > need) blocks = need;
-        k<<<(unsigned)blocks, kBwdWarps * 32, sm, st>>>(fa, va, pix, R, N, C, dLdA);
-    });
-    return cudaGetLastError();
-}
-
-int points_partials(int n) {
-    (void)n;
-    return 4096;
-}
-
-cudaError_t launch_points(const FieldArgs& fa, int n, const float* xyz, const float* mu_gt,
-                          float* mu_out, float* loss_part, int n_part, float* loss_out,
-                          cudaStream_t st) {
-    if (n == 0) return cudaSuccess;
-    const bool fit = mu_gt != nullptr;
-    const size_t sm = fit ? bwd_smem(fa, kBwdWarps) : dense_smem(fa);
-    NH_DISPATCH(fa, {
-        auto k = k_points<D_, TT>;
-        cudaError_t e = set_smem(k, sm);
-        if (e != cudaSuccess) return e;
-        long long blocks;
-        if (fit) {
-            int per_sm = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kBwdWarps * 32, sm);
-            if (per_sm < 1) per_sm = 1;
-            blocks = (long long)num_sms() * per_sm;
-            const long long need = ((long long)n + 32 * kBwdWarps - 1) / (32 * kBwdWarps);
-            if (blocks > need) blocks = need;
-            if (blocks > n_part) blocks = n_part;
-        } else {
-            blocks = ((long long)n + 127) / 128;
-            if (blocks > (long long)num_sms() * 64) blocks = (long long)num_sms() * 64;
-        }
-        k<<<(unsigned)blocks, kBwdWarps * 32, sm, st>>>(fa, n, xyz, mu_gt, mu_out, loss_part);
-        if (fit) {
-            cudaError_t e2 = cudaGetLastError();
-            if (e2 != cudaSuccess) return e2;
-            k_points_loss<<<1, 32, 0, st>>>(loss_part, (int)blocks, n, loss_out, fa.state);
-        }
-    });
-    return cudaGetLastError();
-}
-
-cudaError_t launch_sample_rays(const ViewArgs& va, const int32_t* pix, int R, int N, float* xyz,
-                               float* delta, cudaStream_t st) {
+cudaError_t launch_sample_rays(const ViewArgs& va, const int32_t* pix, int R, int N, float* xyz, float* delta,
+                               cudaStream_t st) {
     const long long n = (long long)R * N;
     if (n == 0) return cudaSuccess;
     k_sample_rays<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(va, pix, R, N, xyz, delta);
@@ -684,27 +100,6 @@ cudaError_t launch_hash_corners(const FieldArgs& fa, int n, const float* xyz, ui
                                 cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     k_hash_corners<<<(n + 127) / 128, 128, 0, st>>>(fa, n, xyz, idx, w);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_encode_points(const FieldArgs& fa, int n, const float* xyz, float* h, cudaStream_t st) {
-    if (n == 0) return cudaSuccess;
-    NH_DISPATCH(fa, { k_encode_points<D_, TT><<<(n + 127) / 128, 128, 0, st>>>(fa, n, xyz, h); });
-    return cudaGetLastError();
-}
-
-cudaError_t launch_query_volume(const FieldArgs& fa, int D, float* out, cudaStream_t st) {
-    const long long n = (long long)D * D * D;
-    if (n == 0) return cudaSuccess;
-    const size_t sm = dense_smem(fa);
-    NH_DISPATCH(fa, {
-        auto k = k_query_volume<D_, TT>;
-        cudaError_t e = set_smem(k, sm);
-        if (e != cudaSuccess) return e;
-        long long blocks = (n + 255) / 256;
-        if (blocks > (long long)num_sms() * 32) blocks = (long long)num_sms() * 32;
-        k<<<(unsigned)blocks, 256, sm, st>>>(fa, D, out);
-    });
     return cudaGetLastError();
 }
 
