@@ -296,6 +296,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                                               a_pred, ws))
     t_bwd = timed(lambda i: nh.render_backward(field, geom, dev_batches[W + i][0], dev_batches[W + i][1], N,
                                                dLdA, ws))
+    launch = nh.launch_info()
     t_adam = timed(lambda i: nh.optimizer_step(field))
     peaks, peak_kind = read_peaks()
     tb = 4 if w.field.precision == S.PREC_F32 else 2
@@ -309,7 +310,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 "peak_source": f"{peak_kind} hbm_gbs",
                 "bytes_per_sample": bytes_per_sample, "units_per_launch": R * N,
                 "launch_ms": {"forward+sum": round(t_fwd, 4), "backward": round(t_bwd, 4),
-                              "adam": round(t_adam, 4)}}
+                              "adam": round(t_adam, 4)},
+                "launch": launch}
 
     # end to end through the host-buffer entry point (pinned host in, loss out)
     pins = [(v, torch.from_numpy(p).pin_memory(), torch.from_numpy(a).pin_memory()) for v, p, a in host_batches]

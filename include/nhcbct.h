@@ -240,6 +240,12 @@ nh_status volume_mse(const float* a_dev, const float* b_dev, int64_t n, double* 
 nh_status project(const nh_geometry* g, const float* vol_dev, int32_t D, int32_t oversample,
                   float* proj_dev, void* stream);
 
+/* Launch configuration of the most recent training-kernel launch in this process
+ * (diagnostics, no paper counterpart): out[0..5] = SM count, CTAs per SM allowed
+ * by registers and shared memory, CTAs per SM allowed by tensor memory, grid size,
+ * TMEM columns per CTA, dynamic shared memory bytes per CTA. n >= 6. */
+nh_status launch_info(int32_t* out, int32_t n);
+
 /* ------------------------------------------------------------------ stage probes
  * The individual stages of the fused kernels, exposed for bitwise tests.
  * sample_rays: positions float[3 * n_rays * n_samples] ([ray][sample][xyz]) and

@@ -591,3 +591,9 @@ extern "C" nh_status volume_mse(const float* a, const float* b, int64_t n, doubl
     NH_CUDA(launch_mse(a, b, n, out_dev, ws, S(stream)), "volume_mse");
     return NH_OK;
 }
+
+extern "C" nh_status launch_info(int32_t* out, int32_t n) {
+    if (!out || n < 6) return fail(NH_ERR_INVALID_ARG, "launch_info: need 6 entries");
+    last_train_grid(out);
+    return NH_OK;
+}

@@ -4,6 +4,11 @@
 
 namespace nh {
 
+GridInfo& last_grid() {
+    static GridInfo g{};
+    return g;
+}
+
 int num_sms() {
     static int n = 0;
     if (n == 0) {
@@ -87,6 +92,16 @@ cudaError_t launch_ray_loss(const float* ray_part, int R, int C, const float* a_
 }
 
 int points_partials(int) { return 4096; }
+
+void last_train_grid(int32_t out[6]) {
+    const GridInfo& g = last_grid();
+    out[0] = g.sms;
+    out[1] = g.occupancy;
+    out[2] = g.by_tmem;
+    out[3] = g.blocks;
+    out[4] = (int32_t)g.tmem_cols;
+    out[5] = (int32_t)g.smem;
+}
 
 cudaError_t launch_sample_rays(const ViewArgs& va, const int32_t* pix, int R, int N, float* xyz, float* delta,
                                cudaStream_t st) {

@@ -602,21 +602,47 @@ static size_t dense_smem(const FieldArgs& fa) {
 // shared memory, and never more than TMEM holds (512 columns per SM), so every
 // CTA's tcgen05.alloc is satisfied without waiting for another CTA to finish.
 template <typename K>
-static long long train_grid(K kernel, size_t smem, uint32_t tcols, long long need) {
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBwdWarps * 32, smem);
-    const int by_tmem = (int)(512u / tcols);
-    if (per_sm > by_tmem) per_sm = by_tmem;
-    if (per_sm < 1) per_sm = 1;
-    long long blocks = (long long)num_sms() * per_sm;
-    return blocks < need ? blocks : need;
-}
+static long long train_grid(K kernel, size_t smem, uint32_t tcols, long long need);
 
+// Opts the kernel into `bytes` of dynamic shared memory and the largest shared
+// memory carveout, so that occupancy queries and launches see the same capacity.
 template <typename K>
 static cudaError_t set_smem(K kernel, size_t bytes) {
-    if (bytes > 48 * 1024)
-        return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    if (bytes > 48 * 1024) {
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+    }
+    return e;
+}
+
+// Last persistent-grid decision of the training kernels (read by launch_info).
+struct GridInfo {
+    int sms, occupancy, by_tmem, blocks;
+    uint32_t tmem_cols;
+    size_t smem;
+};
+GridInfo& last_grid();
+
+template <typename K>
+static long long train_grid(K kernel, size_t smem, uint32_t tcols, long long need) {
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kBwdWarps * 32, smem);
+    const int by_tmem = (int)(512u / tcols);
+    int per_sm = occ < by_tmem ? occ : by_tmem;
+    if (per_sm < 1) per_sm = 1;
+    long long blocks = (long long)num_sms() * per_sm;
+    if (blocks > need) blocks = need;
+    GridInfo& g = last_grid();
+    g.sms = num_sms();
+    g.occupancy = occ;
+    g.by_tmem = by_tmem;
+    g.blocks = (int)blocks;
+    g.tmem_cols = tcols;
+    g.smem = smem;
+    return blocks;
 }
 
 // Dispatch on the feature width D = L * F for a given table type TT.

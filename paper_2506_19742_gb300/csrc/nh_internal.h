@@ -84,6 +84,9 @@ cudaError_t launch_encode_points(const FieldArgs& fa, int n, const float* xyz, f
                                  cudaStream_t st);
 cudaError_t launch_query_volume(const FieldArgs& fa, int D, float* out, cudaStream_t st);
 size_t      mse_workspace_bytes();
+// sms, occupancy (CTAs/SM by registers and shared memory), CTAs/SM by TMEM, grid,
+// TMEM columns per CTA, dynamic shared memory bytes of the last training launch
+void        last_train_grid(int32_t out[6]);
 cudaError_t launch_mse(const float* a, const float* b, int64_t n, double* out, void* ws, cudaStream_t st);
 
 }  // namespace nh

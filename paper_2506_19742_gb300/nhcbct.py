@@ -98,6 +98,7 @@ _SIGS = {
     "query_volume": (_I, [_P, _I, _P, _P]),
     "project": (_I, [_P, _P, _I, _I, _P, _P]),
     "volume_mse": (_I, [_P, _P, C.c_int64, _P, _P, _SZ, _P]),
+    "launch_info": (_I, [C.POINTER(_I), _I]),
     "sample_rays": (_I, [_P, _I, _I, _P, _I, _P, _P, _P]),
     "hash_corners": (_I, [_P, _I, _P, _P, _P, _P]),
     "encode_points": (_I, [_P, _I, _P, _P, _P]),
@@ -379,6 +380,14 @@ def volume_mse(a, b, out=None, stream=None):
     _check(load().volume_mse(_ptr(a), _ptr(b), a.numel(), _ptr(out), _ptr(ws), 8192, _stream(stream)),
            "volume_mse")
     return out
+
+
+def launch_info():
+    """Grid decision of the last training-kernel launch (see include/nhcbct.h)."""
+    out = (C.c_int32 * 6)()
+    _check(load().launch_info(out, 6), "launch_info")
+    keys = ("sms", "ctas_per_sm_occupancy", "ctas_per_sm_tmem", "grid", "tmem_cols", "smem_bytes")
+    return dict(zip(keys, list(out)))
 
 
 def psnr(vol_pred, vol_gt, data_range=1.0, stream=None):
