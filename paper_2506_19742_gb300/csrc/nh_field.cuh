@@ -626,10 +626,31 @@ struct GridInfo {
 };
 GridInfo& last_grid();
 
+// CTAs of `threads` threads that fit on one SM by registers, shared memory and
+// threads, from the compiled kernel's attributes and the device limits.
+template <typename K>
+static int resident_ctas(K kernel, size_t dyn_smem, int threads) {
+    cudaFuncAttributes at;
+    if (cudaFuncGetAttributes(&at, kernel) != cudaSuccess) return 1;
+    int dev = 0, regs_sm = 0, smem_sm = 0, reserved = 0, thr_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+    const int warps = (threads + 31) / 32;
+    const int regs_warp = ((at.numRegs * 32 + 255) / 256) * 256;
+    const int by_regs = regs_warp > 0 ? regs_sm / (regs_warp * warps) : 1;
+    const size_t per_cta = dyn_smem + at.sharedSizeBytes + (size_t)reserved;
+    const int by_smem = (int)((size_t)smem_sm / per_cta);
+    const int by_thr = thr_sm / threads;
+    int n = by_regs < by_smem ? by_regs : by_smem;
+    return n < by_thr ? n : by_thr;
+}
+
 template <typename K>
 static long long train_grid(K kernel, size_t smem, uint32_t tcols, long long need) {
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kBwdWarps * 32, smem);
+    const int occ = resident_ctas(kernel, smem, kBwdWarps * 32);
     const int by_tmem = (int)(512u / tcols);
     int per_sm = occ < by_tmem ? occ : by_tmem;
     if (per_sm < 1) per_sm = 1;
