@@ -91,30 +91,58 @@ __device__ __forceinline__ float adam1(float& p, float& m, float& v, float g, fl
 }
 
 // n must be a multiple of 4; n_lp (a multiple of 4) leading entries refresh lp.
+// Each thread owns kU float4 groups per sweep (strided by the grid so every
+// instruction is coalesced) and issues all of their loads before the first use,
+// so one resident wave keeps enough bytes in flight to stream at HBM speed.
+// Moments and zeroed gradients are written evict-first: only the next optimizer
+// pass reads them, while the parameters stay cacheable for the next gather.
+constexpr int kU = 4;
+
 template <typename LP>
 __global__ void __launch_bounds__(256) k_adam(float* __restrict__ p, float* __restrict__ g,
                                               float* __restrict__ m, float* __restrict__ v, int64_t n,
                                               LP* __restrict__ lp, int64_t n_lp, const DeviceState* st,
                                               float b1, float b2, float eps) {
-    const bool skip = st->skip != 0u;
-    const float inv_scale = st->inv_scale, step_size = st->step_size, ib2 = st->inv_bc2_sqrt;
     const int64_t n4 = n >> 2;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        float4 gg = reinterpret_cast<float4*>(g)[q];
-        reinterpret_cast<float4*>(g)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (skip) continue;
-        float4 pp = reinterpret_cast<float4*>(p)[q];
-        float4 mm = reinterpret_cast<float4*>(m)[q];
-        float4 vv = reinterpret_cast<float4*>(v)[q];
-        adam1(pp.x, mm.x, vv.x, gg.x * inv_scale, b1, b2, eps, step_size, ib2);
-        adam1(pp.y, mm.y, vv.y, gg.y * inv_scale, b1, b2, eps, step_size, ib2);
-        adam1(pp.z, mm.z, vv.z, gg.z * inv_scale, b1, b2, eps, step_size, ib2);
-        adam1(pp.w, mm.w, vv.w, gg.w * inv_scale, b1, b2, eps, step_size, ib2);
-        reinterpret_cast<float4*>(p)[q] = pp;
-        reinterpret_cast<float4*>(m)[q] = mm;
-        reinterpret_cast<float4*>(v)[q] = vv;
-        if ((q << 2) < n_lp) store_lp<LP>(lp, q << 2, pp);
+    const int64_t T = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float4* g4 = reinterpret_cast<float4*>(g);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (st->skip != 0u) {   // skipped step: only the gradients are cleared
+        for (int64_t q = t0; q < n4; q += T) __stcs(g4 + q, z4);
+        return;
+    }
+    const float inv_scale = st->inv_scale, step_size = st->step_size, ib2 = st->inv_bc2_sqrt;
+    float4* p4 = reinterpret_cast<float4*>(p);
+    float4* m4 = reinterpret_cast<float4*>(m);
+    float4* v4 = reinterpret_cast<float4*>(v);
+    for (int64_t base = t0; base < n4; base += T * kU) {
+        float4 gg[kU], pp[kU], mm[kU], vv[kU];
+#pragma unroll
+        for (int u = 0; u < kU; u++) {
+            const int64_t q = base + u * T;
+            if (q < n4) {
+                gg[u] = __ldcs(g4 + q);
+                pp[u] = p4[q];
+                mm[u] = __ldcs(m4 + q);
+                vv[u] = __ldcs(v4 + q);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; u++) {
+            const int64_t q = base + u * T;
+            if (q < n4) {
+                adam1(pp[u].x, mm[u].x, vv[u].x, gg[u].x * inv_scale, b1, b2, eps, step_size, ib2);
+                adam1(pp[u].y, mm[u].y, vv[u].y, gg[u].y * inv_scale, b1, b2, eps, step_size, ib2);
+                adam1(pp[u].z, mm[u].z, vv[u].z, gg[u].z * inv_scale, b1, b2, eps, step_size, ib2);
+                adam1(pp[u].w, mm[u].w, vv[u].w, gg[u].w * inv_scale, b1, b2, eps, step_size, ib2);
+                p4[q] = pp[u];
+                __stcs(m4 + q, mm[u]);
+                __stcs(v4 + q, vv[u]);
+                __stcs(g4 + q, z4);
+                if ((q << 2) < n_lp) store_lp<LP>(lp, q << 2, pp[u]);
+            }
+        }
     }
 }
 
@@ -160,8 +188,15 @@ cudaError_t launch_adam(const FieldArgs& fa, float* params, float* grads, float*
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int64_t n4 = n >> 2;
-    int64_t blocks = (n4 + 255) / 256;
-    const int64_t cap = (int64_t)sm_count() * 8;
+    int64_t blocks = (n4 + 256 * kU - 1) / (256 * kU);
+    int per_sm = 0;   // one resident wave
+    if (fa.precision == NH_PREC_BF16)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adam<__nv_bfloat16>, 256, 0);
+    else if (fa.precision == NH_PREC_F16)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adam<__half>, 256, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adam<float>, 256, 0);
+    const int64_t cap = (int64_t)sm_count() * (per_sm > 0 ? per_sm : 1);
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     if (fa.precision == NH_PREC_BF16)
