@@ -106,16 +106,74 @@ __device__ __forceinline__ float field_mu(const FieldArgs& fa, const float* sp, 
     return mlp_mu<D>(lay, sp, y);
 }
 
+}  // namespace nh
+
+#include "nh_field_mma.cuh"
+
+namespace nh {
+
+// Low-precision tables run the MLP on tensor cores (warp-collective); float tables
+// run the per-thread FFMA MLP.
+template <typename TT>
+constexpr bool kMmaPath = sizeof(TT) == 2;
+
+// Shared-memory carve-up of the forward / query kernels: float dense params, mask,
+// 16-bit weights (tensor-core path) and per-warp tile + row buffer.
+template <typename TT>
+__host__ __device__ inline int fwd_warp_floats() { return kMmaPath<TT> ? kTile16 / 2 + 32 : 0; }
+
+template <typename TT>
+static size_t fwd_smem_bytes(const FieldArgs& fa, int warps) {
+    size_t b = (size_t)(((fa.n_dense + 3) & ~3) + kMaxD) * sizeof(float);
+    if (kMmaPath<TT>) b += (size_t)fa.H * kMmaLayerElems * 2 + (size_t)warps * fwd_warp_floats<TT>() * 4;
+    return b;
+}
+
+struct FwdCta {
+    float *sp, *smask, *wbuf;
+    const uint16_t* sw;
+};
+
+template <typename TT>
+__device__ __forceinline__ FwdCta fwd_begin(const FieldArgs& fa, float* smem) {
+    FwdCta c;
+    const int ndp = (fa.n_dense + 3) & ~3;
+    c.sp = smem;
+    c.smask = c.sp + ndp;
+    uint16_t* sw = reinterpret_cast<uint16_t*>(c.smask + kMaxD);
+    c.sw = sw;
+    c.wbuf = reinterpret_cast<float*>(sw + fa.H * kMmaLayerElems) + (threadIdx.x >> 5) * fwd_warp_floats<TT>();
+    load_dense(fa, c.sp, c.smask);
+    if constexpr (kMmaPath<TT>) {
+        __syncthreads();
+        stage_weights16<TT>(c.sp, DenseLayout{fa.D, fa.H}, fa.D, sw);
+    }
+    __syncthreads();
+    return c;
+}
+
+// mu of this lane's point. On the tensor-core path all 32 lanes must call together.
+template <int D, typename TT>
+__device__ __forceinline__ float point_mu(const FieldArgs& fa, const FwdCta& c, const float x[3], int lane) {
+    if constexpr (kMmaPath<TT>) {
+        float h[D], hhat[D], rstd[D / 2], y[D], C[2][4][4];
+        encode_point<D / 2, TT>(fa, table_base<TT>(fa), x, h);
+        nhe_forward<D>(fa, c.sp, c.smask, h, hhat, rstd, y);
+        uint16_t* tile = reinterpret_cast<uint16_t*>(c.wbuf);
+        float* rowbuf = c.wbuf + kTile16 / 2;
+        return mlp_mu_mma<TT, D, false>(DenseLayout{D, fa.H}, c.sp, c.sw, y, tile, rowbuf, lane, 0u, C);
+    } else {
+        return field_mu<D, TT>(fa, c.sp, c.smask, x);
+    }
+}
+
 // ============================================================================ forward
 template <int D, typename TT>
 __global__ void __launch_bounds__(256) k_ray_forward(FieldArgs fa, ViewArgs va,
                                                      const int32_t* __restrict__ pix, int R, int N,
                                                      int C, float* __restrict__ ray_part) {
     extern __shared__ __align__(16) float smem[];
-    float* sp = smem;
-    float* smask = smem + ((fa.n_dense + 3) & ~3);
-    load_dense(fa, sp, smask);
-    __syncthreads();
+    const FwdCta cta = fwd_begin<TT>(fa, smem);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long task = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
     if (task >= (long long)R * C) return;
@@ -127,10 +185,11 @@ __global__ void __launch_bounds__(256) k_ray_forward(FieldArgs fa, ViewArgs va,
     }
     const int i = c * 32 + lane;
     float mu = 0.f;
-    if (i < N) {
+    if (kMmaPath<TT> || i < N) {
         float x[3];
-        sample_position(g, i, x);
-        mu = field_mu<D, TT>(fa, sp, smask, x);
+        sample_position(g, i < N ? i : N - 1, x);
+        mu = point_mu<D, TT>(fa, cta, x, lane);
+        if (i >= N) mu = 0.f;
     }
     const float s = warp_sum(mu);
     if (lane == 0) ray_part[task] = s * g.delta;
@@ -234,6 +293,55 @@ __device__ __forceinline__ void warp_weight_grad(float* dzb, const float* stage,
     __syncwarp();
 }
 
+// Normalized Hash Encoder backward and the hash scatter of one sample per lane.
+// dh enters as dL/dy and leaves as dL/dh; gamma / beta gradients are reduced across
+// the warp through `col` (32 x 32 floats of per-warp scratch): lane s stores element
+// k of its row at column k ^ s, conflict-free for both the writes and the column sums.
+template <int D>
+__device__ __forceinline__ void nhe_backward_scatter(const FieldArgs& fa, const float* sp, const float* smask,
+                                                     float* sg, float* col, const float (&hhat)[D],
+                                                     const float (&rstd)[D / 2], float (&dh)[D], const float x[3],
+                                                     bool active, int lane) {
+#pragma unroll
+    for (int k = 0; k < D; k++) dh[k] *= smask[k];     // dL/d(gamma hhat + beta)
+    if (fa.norm != NH_NORM_NONE) {
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < D; k++) col[lane * kW + (k ^ lane)] = dh[k] * hhat[k];
+        __syncwarp();
+        if (lane < D) {
+            float s = 0.f;
+#pragma unroll 8
+            for (int t = 0; t < 32; t++) s += col[t * kW + (lane ^ t)];
+            atomicAdd(sg + lane, s);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < D; k++) col[lane * kW + (k ^ lane)] = dh[k];
+        __syncwarp();
+        if (lane < D) {
+            float s = 0.f;
+#pragma unroll 8
+            for (int t = 0; t < 32; t++) s += col[t * kW + (lane ^ t)];
+            atomicAdd(sg + D + lane, s);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < D; k++) dh[k] *= sp[k];   // dL/dhhat
+        if (fa.norm == NH_NORM_LN) {
+            float r1[1] = {rstd[0]};
+            ln_backward<D, D>(hhat, r1, dh);
+        } else {
+            ln_backward<D, 2>(hhat, rstd, dh);
+        }
+    }
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < D; k++) bad |= !isfinite(dh[k]);
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&fa.state->flags, NH_FLAG_NONFINITE);
+    if (active) scatter_point<D / 2>(fa, x, dh);
+}
+
 // Forward with activations kept in TMEM, then the full backward of one sample per
 // lane. dmu_of(mu) gives dL/dmu (already multiplied by the loss scale); inactive
 // lanes use dmu = 0 and skip the scatter. All 32 lanes must call it together.
@@ -323,62 +431,64 @@ __device__ __forceinline__ float sample_fwd_bwd(const FieldArgs& fa, const float
     }
     float dh[D];
     linear_bwd_data<D, kW>(sp + lay.W(0), dz, dh);   // dh <- dL/dy
-#pragma unroll
-    for (int k = 0; k < D; k++) dh[k] *= smask[k];     // dL/d(gamma hhat + beta)
-
-    if (affine) {
-        // dgamma_k = sum_s dy'_k hhat_k, dbeta_k = sum_s dy'_k, transposed through dzb:
-        // lane s stores element k of its row at column k ^ s (conflict-free both ways).
-        float* col = dzb;
-#pragma unroll
-        for (int k = 0; k < D; k++) col[lane * kW + (k ^ lane)] = dh[k] * hhat[k];
-        __syncwarp();
-        if (lane < D) {
-            float s = 0.f;
-#pragma unroll 8
-            for (int t = 0; t < 32; t++) s += col[t * kW + (lane ^ t)];
-            atomicAdd(sg + lane, s);
-        }
-        __syncwarp();
-#pragma unroll
-        for (int k = 0; k < D; k++) col[lane * kW + (k ^ lane)] = dh[k];
-        __syncwarp();
-        if (lane < D) {
-            float s = 0.f;
-#pragma unroll 8
-            for (int t = 0; t < 32; t++) s += col[t * kW + (lane ^ t)];
-            atomicAdd(sg + D + lane, s);
-        }
-        __syncwarp();
-#pragma unroll
-        for (int k = 0; k < D; k++) dh[k] *= sp[k];   // dL/dhhat
-        if (fa.norm == NH_NORM_LN) {
-            float r1[1] = {rstd[0]};
-            ln_backward<D, D>(hhat, r1, dh);
-        } else {
-            ln_backward<D, 2>(hhat, rstd, dh);
-        }
-    }
-    bool bad = false;
-#pragma unroll
-    for (int k = 0; k < D; k++) bad |= !isfinite(dh[k]);
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&fa.state->flags, NH_FLAG_NONFINITE);
-    if (active) scatter_point<L>(fa, x, dh);
+    nhe_backward_scatter<D>(fa, sp, smask, sg, dzb, hhat, rstd, dh, x, active, lane);
     return mu;
 }
 
-// TMEM columns per CTA: two lane-quarter groups of warps, 32 H columns per thread.
+// Mixed-precision counterpart of sample_fwd_bwd: the MLP of the warp's 32 samples
+// runs on tensor cores (nh_field_mma.cuh); encoding, normalization, LN backward and
+// the scatter are the per-sample float32 code. All 32 lanes must call it together.
+template <int D, typename TT, class DmuFn>
+__device__ __forceinline__ float sample_fwd_bwd_mma(const FieldArgs& fa, const float* sp, const uint16_t* sw,
+                                                    const float* smask, float* sg, float* wbuf, uint32_t tslot0,
+                                                    const float x[3], bool active, int lane, DmuFn dmu_of) {
+    constexpr int L = D / 2;
+    const DenseLayout lay{D, fa.H};
+    uint16_t* tile = reinterpret_cast<uint16_t*>(wbuf);
+    uint16_t* dztile = tile + kTile16;
+    float* rowbuf = reinterpret_cast<float*>(dztile + kTile16);
+    float rstd[D / 2];
+    float C[2][4][4];
+    float mu;
+    {
+        float h[D], hhat[D], y[D];
+        encode_point<L, TT>(fa, table_base<TT>(fa), x, h);
+        nhe_forward<D>(fa, sp, smask, h, hhat, rstd, y);
+        tmem_st(tslot0, hhat);
+        mu = mlp_mu_mma<TT, D, true>(lay, sp, sw, y, tile, rowbuf, lane, tslot0 + 32, C);
+    }
+    const float dmu = active ? dmu_of(mu) : 0.f;
+    const float dzo = dmu * mu * (1.f - mu);
+    float dz[2][4][4];
+    out_layer_backward_mma<4>(lay, sp, sg, rowbuf, lane, dzo, C, dz);
+    float dh[D];
+    mlp_backward_mma<TT, D>(lay, sw, sg, tile, dztile, lane, tslot0 + 32, dz, dh);
+    float hhat[D];
+    tmem_ld(tslot0, hhat);
+    nhe_backward_scatter<D>(fa, sp, smask, sg, wbuf, hhat, rstd, dh, x, active, lane);
+    return mu;
+}
+
+// TMEM columns of one thread: FFMA path 32 H (hhat, a_1 .. a_{H-1}); tensor-core
+// path 32 + 16 H (hhat, then A fragments of every layer input).
+__host__ __device__ inline int bwd_cols_per_thread(int precision, int H) {
+    return precision == NH_PREC_F32 ? 32 * H : mma_tmem_cols_per_thread(H);
+}
+// TMEM columns per CTA: two lane-quarter groups of warps, rounded to a power of two.
 static uint32_t bwd_tmem_cols(const FieldArgs& fa) {
-    uint32_t need = (uint32_t)(kBwdWarps / 4) * 32u * (uint32_t)fa.H, c = 32;
+    uint32_t need = (uint32_t)(kBwdWarps / 4) * (uint32_t)bwd_cols_per_thread(fa.precision, fa.H), c = 32;
     while (c < need) c <<= 1;
     return c;
 }
-// Shared memory of the backward kernels (bytes). Registers cap residency at two
-// CTAs per SM; when one CTA takes all 512 TMEM columns the request is padded so
-// that only one CTA fits, and no tcgen05.alloc waits on a resident CTA.
+// Shared memory of the backward kernels (bytes): float dense params, mask, gradient
+// accumulators, 16-bit weights (tensor-core path) and 8 warps of scratch. Registers
+// cap residency at two CTAs per SM; when one CTA takes all 512 TMEM columns the
+// request is padded so that only one CTA fits, and no tcgen05.alloc waits on a
+// resident CTA.
 static size_t bwd_smem_bytes(const FieldArgs& fa) {
     const int ndp = (fa.n_dense + 3) & ~3;
     size_t b = (size_t)(2 * ndp + kMaxD + kBwdWarps * warp_scratch_floats()) * sizeof(float);
+    if (fa.precision != NH_PREC_F32) b += (size_t)fa.H * kMmaLayerElems * 2;
     if (512u / bwd_tmem_cols(fa) < 2u && b < 120 * 1024) b = 120 * 1024;
     return b;
 }
@@ -386,9 +496,11 @@ static size_t bwd_smem_bytes(const FieldArgs& fa) {
 // CTA prologue / epilogue shared by the training kernels.
 struct BwdCta {
     float *sp, *smask, *sg, *wbuf;
+    const uint16_t* sw;
     uint32_t tbase, tslot0;
 };
 
+template <typename TT>
 __device__ __forceinline__ BwdCta bwd_begin(const FieldArgs& fa, float* smem, uint32_t* s_tmem, uint32_t tcols) {
     BwdCta c;
     const int ndp = (fa.n_dense + 3) & ~3;
@@ -397,15 +509,31 @@ __device__ __forceinline__ BwdCta bwd_begin(const FieldArgs& fa, float* smem, ui
     c.smask = c.sp + ndp;
     c.sg = c.smask + kMaxD;
     c.wbuf = c.sg + ndp + warp * warp_scratch_floats();
+    uint16_t* sw = reinterpret_cast<uint16_t*>(c.sg + ndp + kBwdWarps * warp_scratch_floats());
+    c.sw = sw;
     if (warp == 0) tmem_alloc(s_tmem, tcols);
     load_dense(fa, c.sp, c.smask);
     for (int k = threadIdx.x; k < ndp; k += blockDim.x) c.sg[k] = 0.f;
+    if constexpr (kMmaPath<TT>) {
+        __syncthreads();
+        stage_weights16<TT>(c.sp, DenseLayout{fa.D, fa.H}, fa.D, sw);
+    }
     tmem_fence_before_sync();
     __syncthreads();
     tmem_fence_after_sync();
     c.tbase = *s_tmem;
-    c.tslot0 = tmem_lane_addr(c.tbase, warp, (warp >> 2) * 32 * fa.H);
+    c.tslot0 = tmem_lane_addr(c.tbase, warp, (warp >> 2) * bwd_cols_per_thread(fa.precision, fa.H));
     return c;
+}
+
+// One training sample per lane through the FFMA or the tensor-core MLP.
+template <int D, typename TT, class DmuFn>
+__device__ __forceinline__ float train_sample(const FieldArgs& fa, const BwdCta& c, const float x[3], bool active,
+                                              int lane, DmuFn dmu_of) {
+    if constexpr (kMmaPath<TT>)
+        return sample_fwd_bwd_mma<D, TT>(fa, c.sp, c.sw, c.smask, c.sg, c.wbuf, c.tslot0, x, active, lane, dmu_of);
+    else
+        return sample_fwd_bwd<D, TT>(fa, c.sp, c.smask, c.sg, c.wbuf, c.tslot0, x, active, lane, dmu_of);
 }
 
 __device__ __forceinline__ void bwd_end(const FieldArgs& fa, const BwdCta& c, uint32_t tcols) {
@@ -428,7 +556,7 @@ k_ray_backward(FieldArgs fa, ViewArgs va, const int32_t* __restrict__ pix, int R
                const float* __restrict__ dLdA, uint32_t tcols) {
     extern __shared__ __align__(16) float smem[];
     __shared__ uint32_t s_tmem;
-    const BwdCta cta = bwd_begin(fa, smem, &s_tmem, tcols);
+    const BwdCta cta = bwd_begin<TT>(fa, smem, &s_tmem, tcols);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const float scale = fa.state->loss_scale;
     const long long ntask = (long long)R * C;
@@ -442,26 +570,29 @@ k_ray_backward(FieldArgs fa, ViewArgs va, const int32_t* __restrict__ pix, int R
         float x[3];
         sample_position(g, active ? i : N - 1, x);
         const float gr = dLdA[r] * g.delta * scale;
-        sample_fwd_bwd<D, TT>(fa, cta.sp, cta.smask, cta.sg, cta.wbuf, cta.tslot0, x, active, lane,
-                              [gr](float) { return gr; });
+        train_sample<D, TT>(fa, cta, x, active, lane, [gr](float) { return gr; });
     }
     bwd_end(fa, cta, tcols);
 }
 
 // ============================================================================ points
 // query: mu_out[p] = M(x_p), forward only.
+// Warps take 32 consecutive points; lanes past the end evaluate the last point and
+// discard it (the tensor-core MLP needs every lane).
 template <int D, typename TT>
 __global__ void __launch_bounds__(128) k_points(FieldArgs fa, int n, const float* __restrict__ xyz,
                                                 float* __restrict__ mu_out) {
     extern __shared__ __align__(16) float smem[];
-    float* sp = smem;
-    float* smask = sp + ((fa.n_dense + 3) & ~3);
-    load_dense(fa, sp, smask);
-    __syncthreads();
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
-         p += (long long)gridDim.x * blockDim.x) {
-        const float x[3] = {xyz[3 * p], xyz[3 * p + 1], xyz[3 * p + 2]};
-        mu_out[p] = field_mu<D, TT>(fa, sp, smask, x);
+    const FwdCta cta = fwd_begin<TT>(fa, smem);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long ntask = ((long long)n + 31) / 32;
+    for (long long task = (long long)blockIdx.x * (blockDim.x >> 5) + warp; task < ntask;
+         task += (long long)gridDim.x * (blockDim.x >> 5)) {
+        const long long p = task * 32 + lane;
+        const long long pc = p < n ? p : (long long)n - 1;
+        const float x[3] = {xyz[3 * pc], xyz[3 * pc + 1], xyz[3 * pc + 2]};
+        const float mu = point_mu<D, TT>(fa, cta, x, lane);
+        if (p < n) mu_out[p] = mu;
     }
 }
 
@@ -474,7 +605,7 @@ k_points_fit(FieldArgs fa, int n, const float* __restrict__ xyz, const float* __
     extern __shared__ __align__(16) float smem[];
     __shared__ uint32_t s_tmem;
     __shared__ float red[kBwdWarps];
-    const BwdCta cta = bwd_begin(fa, smem, &s_tmem, tcols);
+    const BwdCta cta = bwd_begin<TT>(fa, smem, &s_tmem, tcols);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float lsum = 0.f;
     const float scale = fa.state->loss_scale / (float)n;
@@ -486,11 +617,10 @@ k_points_fit(FieldArgs fa, int n, const float* __restrict__ xyz, const float* __
         const long long pc = active ? p : (long long)n - 1;
         const float x[3] = {xyz[3 * pc], xyz[3 * pc + 1], xyz[3 * pc + 2]};
         const float gt = mu_gt[pc];
-        const float mu = sample_fwd_bwd<D, TT>(fa, cta.sp, cta.smask, cta.sg, cta.wbuf, cta.tslot0, x, active,
-                                               lane, [gt, scale](float m) {
-                                                   const float r = m - gt;
-                                                   return (r > 0.f ? scale : (r < 0.f ? -scale : 0.f));
-                                               });
+        const float mu = train_sample<D, TT>(fa, cta, x, active, lane, [gt, scale](float m) {
+            const float r = m - gt;
+            return (r > 0.f ? scale : (r < 0.f ? -scale : 0.f));
+        });
         if (active) lsum += fabsf(mu - gt);
     }
     bwd_end(fa, cta, tcols);
@@ -575,19 +705,21 @@ static __global__ void k_voxel_centres(int D, float* __restrict__ xyz) {
 template <int D_, typename TT>
 __global__ void __launch_bounds__(256) k_query_volume(FieldArgs fa, int D, float* __restrict__ out) {
     extern __shared__ __align__(16) float smem[];
-    float* sp = smem;
-    float* smask = smem + ((fa.n_dense + 3) & ~3);
-    load_dense(fa, sp, smask);
-    __syncthreads();
+    const FwdCta cta = fwd_begin<TT>(fa, smem);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long n = (long long)D * D * D;
+    const long long ntask = (n + 31) / 32;
     const float fD = (float)D;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
-         t += (long long)gridDim.x * blockDim.x) {
-        const int xi = (int)(t % D), yi = (int)((t / D) % D), zi = (int)(t / ((long long)D * D));
+    for (long long task = (long long)blockIdx.x * (blockDim.x >> 5) + warp; task < ntask;
+         task += (long long)gridDim.x * (blockDim.x >> 5)) {
+        const long long t = task * 32 + lane;
+        const long long tc = t < n ? t : n - 1;
+        const int xi = (int)(tc % D), yi = (int)((tc / D) % D), zi = (int)(tc / ((long long)D * D));
         const float x[3] = {__fdiv_rn(__fadd_rn((float)xi, 0.5f), fD),
                             __fdiv_rn(__fadd_rn((float)yi, 0.5f), fD),
                             __fdiv_rn(__fadd_rn((float)zi, 0.5f), fD)};
-        out[t] = field_mu<D_, TT>(fa, sp, smask, x);
+        const float mu = point_mu<D_, TT>(fa, cta, x, lane);
+        if (t < n) out[t] = mu;
     }
 }
 
@@ -681,7 +813,7 @@ cudaError_t launch_ray_forward_tt(const FieldArgs& fa, const ViewArgs& va, const
     const long long tasks = (long long)R * C;
     if (tasks == 0) return cudaSuccess;
     const long long blocks = (tasks + 7) / 8;
-    const size_t sm = dense_smem(fa);
+    const size_t sm = fwd_smem_bytes<TT>(fa, 8);
     NH_DISPATCH_D(fa, {
         auto k = k_ray_forward<D_, TT>;
         cudaError_t e = set_smem(k, sm);
@@ -714,7 +846,7 @@ cudaError_t launch_points_tt(const FieldArgs& fa, int n, const float* xyz, const
                              float* loss_part, int n_part, float* loss_out, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     if (mu_gt == nullptr) {
-        const size_t sm = dense_smem(fa);
+        const size_t sm = fwd_smem_bytes<TT>(fa, 4);
         NH_DISPATCH_D(fa, {
             auto k = k_points<D_, TT>;
             cudaError_t e = set_smem(k, sm);
@@ -752,7 +884,7 @@ template <typename TT>
 cudaError_t launch_query_volume_tt(const FieldArgs& fa, int D, float* out, cudaStream_t st) {
     const long long n = (long long)D * D * D;
     if (n == 0) return cudaSuccess;
-    const size_t sm = dense_smem(fa);
+    const size_t sm = fwd_smem_bytes<TT>(fa, 8);
     NH_DISPATCH_D(fa, {
         auto k = k_query_volume<D_, TT>;
         cudaError_t e = set_smem(k, sm);
