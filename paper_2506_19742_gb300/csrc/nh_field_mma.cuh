@@ -167,10 +167,30 @@ __device__ __forceinline__ void mlp_backward_mma(const DenseLayout& lay, const u
         const uint16_t* Wt = Wn + 32 * kWS;
         const bool first = (l == 0);
         const int IN = first ? D : kW;
-        // db_l and the 16-bit dz tile (A fragments of dz, reused for the data gradient)
+        // db_l; dz as hi + lo 16-bit fragments: the data gradient uses both (so the
+        // rounding does not compound along the chain), the dz tile holds hi
         add_colsum<4>(dz, sg + lay.b(l), lane);
         uint32_t Adz[2][2][4];
-        pack_afrag<T>(dz, Adz);
+        float din[2][4][4];
+        {
+            uint32_t Adl[2][2][4];
+            pack_afrag_split<T>(dz, Adz, Adl);
+            // data gradient din[s][i] = sum_j dz[s][j] W[j][i]  (B = W^T rows)
+            if (first && D == 16) {
+                float d2[2][2][4];
+                mma_layer<T, 2, 2>(Wt, nullptr, Adz, lane, d2);
+                mma_accumulate<T, 2, 2>(Wt, Adl, lane, d2);
+#pragma unroll
+                for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+                    for (int nt = 0; nt < 4; nt++)
+#pragma unroll
+                        for (int c = 0; c < 4; c++) din[mt][nt][c] = nt < 2 ? d2[mt][nt][c] : 0.f;
+            } else {
+                mma_layer<T, 2, 4>(Wt, nullptr, Adz, lane, din);
+                mma_accumulate<T, 2, 4>(Wt, Adl, lane, din);
+            }
+        }
         // layer input fragments from tensor memory
         uint32_t Aact[2][2][4];
         tm_ld_u32<16>(tcol0 + 16 * l, &Aact[0][0][0]);
@@ -187,66 +207,47 @@ __device__ __forceinline__ void mlp_backward_mma(const DenseLayout& lay, const u
             store_afrag<2>(tile, lane, Aact);
         }
         __syncwarp();
-        // dW_l[j][i] = sum_s dz[s][j] act[s][i]: A = dz^T (m = j, k = s), B = act (k = s, n = i)
+        // dW_l[j][i] = sum_s dz[s][j] act[s][i]: A = dz^T (m = j, k = s), B = act (k = s, n = i),
+        // one 16-row half of j at a time
         {
-            uint32_t AdT[2][2][4];
-#pragma unroll
-            for (int mj = 0; mj < 2; mj++)
+            float* gW = sg + lay.W(l);
+            const int NP = IN / 16;
+#pragma unroll 1
+            for (int mj = 0; mj < 2; mj++) {
+                uint32_t AdT[2][4];
 #pragma unroll
                 for (int ks = 0; ks < 2; ks++) {
                     const int s_off = (q >> 1) * 8, j_off = (q & 1) * 8;
-                    ldsm_x4_trans(AdT[mj][ks], dztile + (16 * ks + s_off + r8) * kWS + 16 * mj + j_off);
+                    ldsm_x4_trans(AdT[ks], dztile + (16 * ks + s_off + r8) * kWS + 16 * mj + j_off);
                 }
-            float dW[2][4][4];
-#pragma unroll
-            for (int mj = 0; mj < 2; mj++)
+                float dW[4][4];
 #pragma unroll
                 for (int nt = 0; nt < 4; nt++)
 #pragma unroll
-                    for (int c = 0; c < 4; c++) dW[mj][nt][c] = 0.f;
-            const int NP = IN / 16;
+                    for (int c = 0; c < 4; c++) dW[nt][c] = 0.f;
 #pragma unroll
-            for (int ks = 0; ks < 2; ks++)
+                for (int ks = 0; ks < 2; ks++)
 #pragma unroll
-                for (int np = 0; np < 2; np++) {
-                    if (np < NP) {
-                        uint32_t Bq[4];
-                        const int s_off = (q & 1) * 8, i_off = (q >> 1) * 8;
-                        ldsm_x4_trans(Bq, tile + (16 * ks + s_off + r8) * kWS + 16 * np + i_off);
-#pragma unroll
-                        for (int mj = 0; mj < 2; mj++) {
-                            Mma<T>::mma(dW[mj][2 * np], AdT[mj][ks], Bq[0], Bq[1]);
-                            Mma<T>::mma(dW[mj][2 * np + 1], AdT[mj][ks], Bq[2], Bq[3]);
+                    for (int np = 0; np < 2; np++) {
+                        if (np < NP) {
+                            uint32_t Bq[4];
+                            const int s_off = (q & 1) * 8, i_off = (q >> 1) * 8;
+                            ldsm_x4_trans(Bq, tile + (16 * ks + s_off + r8) * kWS + 16 * np + i_off);
+                            Mma<T>::mma(dW[2 * np], AdT[ks], Bq[0], Bq[1]);
+                            Mma<T>::mma(dW[2 * np + 1], AdT[ks], Bq[2], Bq[3]);
                         }
                     }
-                }
-            float* gW = sg + lay.W(l);
-#pragma unroll
-            for (int mj = 0; mj < 2; mj++)
 #pragma unroll
                 for (int nt = 0; nt < 4; nt++) {
                     if (nt < IN / 8) {
 #pragma unroll
                         for (int c = 0; c < 4; c++) {
                             const int j = 16 * mj + g + 8 * (c >> 1), i = 8 * nt + 2 * t + (c & 1);
-                            atomicAdd(gW + j * IN + i, dW[mj][nt][c]);
+                            atomicAdd(gW + j * IN + i, dW[nt][c]);
                         }
                     }
                 }
-        }
-        // data gradient din[s][i] = sum_j dz[s][j] W[j][i]  (B = W^T rows)
-        float din[2][4][4];
-        if (first && D == 16) {
-            float d2[2][2][4];
-            mma_layer<T, 2, 2>(Wt, nullptr, Adz, lane, d2);
-#pragma unroll
-            for (int mt = 0; mt < 2; mt++)
-#pragma unroll
-                for (int nt = 0; nt < 4; nt++)
-#pragma unroll
-                    for (int c = 0; c < 4; c++) din[mt][nt][c] = nt < 2 ? d2[mt][nt][c] : 0.f;
-        } else {
-            mma_layer<T, 2, 4>(Wt, nullptr, Adz, lane, din);
+            }
         }
         if (!first) {
             // ReLU mask of layer l's input, read from its A fragments

@@ -134,6 +134,62 @@ __device__ __forceinline__ void mma_layer(const uint16_t* Wn, const float* bias,
         }
 }
 
+// C[mt][nt] += sum_ks A[mt][ks] B[ks][nt] (no bias, accumulate).
+template <typename T, int KS, int NT>
+__device__ __forceinline__ void mma_accumulate(const uint16_t* Wn, const uint32_t (&A)[2][KS][4], int lane,
+                                               float (&Cf)[2][NT][4]) {
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int ks = 0; ks < KS; ks++)
+#pragma unroll
+        for (int nt = 0; nt < NT; nt++) {
+            const uint16_t* w = Wn + (8 * nt + g) * kWS + 16 * ks + 2 * t;
+            const uint32_t b0 = *reinterpret_cast<const uint32_t*>(w);
+            const uint32_t b1 = *reinterpret_cast<const uint32_t*>(w + 8);
+#pragma unroll
+            for (int mt = 0; mt < 2; mt++) Mma<T>::mma(Cf[mt][nt], A[mt][ks], b0, b1);
+        }
+}
+
+// 16-bit value of x and the 16-bit rounding of its remainder: x ~ hi + lo with
+// about twice the mantissa bits of one 16-bit value.
+template <typename T>
+__device__ __forceinline__ void split16(float x, uint16_t& hi, uint16_t& lo);
+template <>
+__device__ __forceinline__ void split16<__nv_bfloat16>(float x, uint16_t& hi, uint16_t& lo) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+    hi = *reinterpret_cast<const uint16_t*>(&h);
+    lo = *reinterpret_cast<const uint16_t*>(&l);
+}
+template <>
+__device__ __forceinline__ void split16<__half>(float x, uint16_t& hi, uint16_t& lo) {
+    const __half h = __float2half_rn(x);
+    const __half l = __float2half_rn(x - __half2float(h));
+    hi = *reinterpret_cast<const uint16_t*>(&h);
+    lo = *reinterpret_cast<const uint16_t*>(&l);
+}
+
+// Pack C fragments into hi and lo A fragments (x ~ hi + lo).
+template <typename T>
+__device__ __forceinline__ void pack_afrag_split(const float (&Cf)[2][4][4], uint32_t (&Ah)[2][2][4],
+                                                 uint32_t (&Al)[2][2][4]) {
+#pragma unroll
+    for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+        for (int ks = 0; ks < 2; ks++)
+#pragma unroll
+            for (int r = 0; r < 4; r++) {
+                const float* src = Cf[mt][2 * ks + (r >> 1)];
+                const int e = (r & 1) * 2;
+                uint16_t h0, l0, h1, l1;
+                split16<T>(src[e], h0, l0);
+                split16<T>(src[e + 1], h1, l1);
+                Ah[mt][ks][r] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+                Al[mt][ks][r] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+            }
+}
+
 // ReLU and pack C fragments (32 outputs) into next-layer A fragments (K = 32).
 template <typename T>
 __device__ __forceinline__ void relu_pack(const float (&Cf)[2][4][4], uint32_t (&A)[2][2][4]) {
