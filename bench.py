@@ -292,12 +292,17 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         return float(np.mean([a.elapsed_time(b) for a, b in evs]))
 
     dLdA = torch.full((R,), 1e-3, device=dev)
-    t_fwd = timed(lambda i: nh.render_forward(field, geom, dev_batches[W + i][0], dev_batches[W + i][1], N,
-                                              a_pred, ws))
-    t_bwd = timed(lambda i: nh.render_backward(field, geom, dev_batches[W + i][0], dev_batches[W + i][1], N,
-                                               dLdA, ws))
-    launch = nh.launch_info()
-    t_adam = timed(lambda i: nh.optimizer_step(field))
+
+    def kernel_ms(fld, wsp):
+        t_f = timed(lambda i: nh.render_forward(fld, geom, dev_batches[W + i][0], dev_batches[W + i][1], N,
+                                                a_pred, wsp))
+        t_b = timed(lambda i: nh.render_backward(fld, geom, dev_batches[W + i][0], dev_batches[W + i][1], N,
+                                                 dLdA, wsp))
+        info = nh.launch_info()
+        t_a = timed(lambda i: nh.optimizer_step(fld))
+        return t_f, t_b, t_a, info
+
+    t_fwd, t_bwd, t_adam, launch = kernel_ms(field, ws)
     peaks, peak_kind = read_peaks()
     tb = 4 if w.field.precision == S.PREC_F32 else 2
     L, F = w.field.n_levels, w.field.n_feat
@@ -338,10 +343,12 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if args.mixed and args.mixed != args.workload:
         wm = S.WORKLOADS[args.mixed]
         if wm.n_rays == R and wm.n_samples == N and wm.geometry == w.geometry:
-            _, _, ms_m = measure(wm)
+            field_m, ws_m, ms_m = measure(wm)
             ms_m = allmax(ms_m)
+            tf, tbk, ta, _ = kernel_ms(field_m, ws_m)
             mixed = {"workload": wm.name, "value": samples_all / (ms_m / 1e3), "unit": UNIT,
-                     "ms_per_step": ms_m / K, "speedup_vs_fp32": (samples_all / (ms_m / 1e3)) / value}
+                     "ms_per_step": ms_m / K, "speedup_vs_fp32": (samples_all / (ms_m / 1e3)) / value,
+                     "launch_ms": {"forward+sum": round(tf, 4), "backward": round(tbk, 4), "adam": round(ta, 4)}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
