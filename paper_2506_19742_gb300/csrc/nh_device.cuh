@@ -161,10 +161,17 @@ __device__ __forceinline__ void red_add_f2(float* addr, float a, float b) {
     atomicAdd(reinterpret_cast<float2*>(addr), make_float2(a, b));
 }
 
+// Scatter of one sample per lane; all 32 lanes of the warp call it together, and
+// lanes whose sample must not contribute pass zeros in dh. Consecutive lanes hold
+// consecutive samples of one ray, so lanes in the same cell of a level form one
+// contiguous run: where a level has such runs, each run is summed with a segmented
+// shuffle reduction (per corner and feature) and only its first lane issues the 8
+// vector atomics. Levels whose cells are all distinct scatter directly.
+// dhrow: this lane's dL/dh (2 L floats, in shared memory).
 template <int L>
-__device__ __forceinline__ void scatter_point(const FieldArgs& fa, const float x[3], const float (&dh)[2 * L]) {
+__device__ __forceinline__ void scatter_point(const FieldArgs& fa, const float x[3], const float* dhrow, int lane) {
     const size_t T = (size_t)fa.Tmask + 1;
-#pragma unroll
+#pragma unroll 1
     for (int l = 0; l < L; l++) {
         uint32_t c[3];
         float w[3];
@@ -172,12 +179,37 @@ __device__ __forceinline__ void scatter_point(const FieldArgs& fa, const float x
         level_cell(x, res, c, w);
         const bool dense = (fa.dense_mask >> l) & 1u;
         const uint32_t stride = (uint32_t)res + 1u;
+        const float d0 = dhrow[2 * l], d1 = dhrow[2 * l + 1];
+        const uint32_t px = __shfl_up_sync(0xffffffffu, c[0], 1);
+        const uint32_t py = __shfl_up_sync(0xffffffffu, c[1], 1);
+        const uint32_t pz = __shfl_up_sync(0xffffffffu, c[2], 1);
+        const bool head = lane == 0 || px != c[0] || py != c[1] || pz != c[2];
+        const uint32_t heads = __ballot_sync(0xffffffffu, head);
+        float v[16];
+        uint32_t idx[8];
 #pragma unroll
         for (int k = 0; k < 8; k++) {
-            uint32_t idx;
             float wk;
-            corner(c, w, k, stride, dense, fa.Tmask, idx, wk);
-            red_add_f2(fa.grads + ((size_t)l * T + idx) * 2, wk * dh[2 * l], wk * dh[2 * l + 1]);
+            corner(c, w, k, stride, dense, fa.Tmask, idx[k], wk);
+            v[2 * k] = wk * d0;
+            v[2 * k + 1] = wk * d1;
+        }
+        if (heads != 0xffffffffu) {
+            const uint32_t after = lane == 31 ? 0u : (heads & (0xffffffffu << (lane + 1)));
+            const int seg_end = after ? (__ffs(after) - 2) : 31;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+                for (int e = 0; e < 16; e++) {
+                    const float t = __shfl_down_sync(0xffffffffu, v[e], off);
+                    if (lane + off <= seg_end) v[e] += t;
+                }
+            }
+        }
+        if (head) {
+            float* gl = fa.grads + (size_t)l * T * 2;
+#pragma unroll
+            for (int k = 0; k < 8; k++) red_add_f2(gl + (size_t)idx[k] * 2, v[2 * k], v[2 * k + 1]);
         }
     }
 }
