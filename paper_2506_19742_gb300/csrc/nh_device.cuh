@@ -167,7 +167,7 @@ __device__ __forceinline__ void red_add_f2(float* addr, float a, float b) {
 // contiguous run: where a level has such runs, each run is summed with a segmented
 // shuffle reduction (per corner and feature) and only its first lane issues the 8
 // vector atomics. Levels whose cells are all distinct scatter directly.
-// dhrow: this lane's dL/dh (2 L floats, in shared memory).
+// dhrow: this lane's dL/dh in shared memory, element k at dhrow[k ^ lane] (2 L <= 32).
 template <int L>
 __device__ __forceinline__ void scatter_point(const FieldArgs& fa, const float x[3], const float* dhrow, int lane) {
     const size_t T = (size_t)fa.Tmask + 1;
@@ -179,7 +179,7 @@ __device__ __forceinline__ void scatter_point(const FieldArgs& fa, const float x
         level_cell(x, res, c, w);
         const bool dense = (fa.dense_mask >> l) & 1u;
         const uint32_t stride = (uint32_t)res + 1u;
-        const float d0 = dhrow[2 * l], d1 = dhrow[2 * l + 1];
+        const float d0 = dhrow[(2 * l) ^ lane], d1 = dhrow[(2 * l + 1) ^ lane];
         const uint32_t px = __shfl_up_sync(0xffffffffu, c[0], 1);
         const uint32_t py = __shfl_up_sync(0xffffffffu, c[1], 1);
         const uint32_t pz = __shfl_up_sync(0xffffffffu, c[2], 1);

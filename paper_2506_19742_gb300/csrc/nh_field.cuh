@@ -339,11 +339,12 @@ __device__ __forceinline__ void nhe_backward_scatter(const FieldArgs& fa, const 
 #pragma unroll
     for (int k = 0; k < D; k++) bad |= !isfinite(dh[k]);
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&fa.state->flags, NH_FLAG_NONFINITE);
-    // the scatter is warp-collective: lanes without a sample contribute zeros
-    float* row = col + lane * (kW + 1);
+    // the scatter is warp-collective: lanes without a sample contribute zeros; the
+    // row (32 floats of the 32 x 32 scratch) holds element k at column k ^ lane
+    float* row = col + lane * kW;
     __syncwarp();
 #pragma unroll
-    for (int k = 0; k < D; k++) row[k] = active ? dh[k] : 0.f;
+    for (int k = 0; k < D; k++) row[k ^ lane] = active ? dh[k] : 0.f;
     scatter_point<D / 2>(fa, x, row, lane);
 }
 
