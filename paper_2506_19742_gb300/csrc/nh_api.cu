@@ -7,6 +7,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -596,4 +597,48 @@ extern "C" nh_status launch_info(int32_t* out, int32_t n) {
     if (!out || n < 6) return fail(NH_ERR_INVALID_ARG, "launch_info: need 6 entries");
     last_train_grid(out);
     return NH_OK;
+}
+
+// ----------------------------------------------------------------------------- fixed-scratch forward
+// render_forward_noalloc takes its scratch from this fixed block of device memory
+// instead of a caller workspace. The block is part of the library image: every GPU
+// on which the library is used holds it until the process exits. In host code the
+// name g_fixed_ws only stands for the variable; the device address is looked up
+// with cudaGetSymbolAddress, once per device, with that device current.
+constexpr size_t kFixedWsBytes = size_t(1) << 20;
+static __device__ __align__(256) unsigned char g_fixed_ws[kFixedWsBytes];
+
+static std::mutex g_fixed_mu;
+static void* g_fixed_ptr[64];
+
+static nh_status fixed_workspace(void** out) {
+    int dev = 0;
+    NH_CUDA(cudaGetDevice(&dev), "render_forward_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(NH_ERR_UNSUPPORTED, "render_forward_noalloc: device ordinal %d >= 64", dev);
+    std::lock_guard<std::mutex> lock(g_fixed_mu);
+    if (!g_fixed_ptr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_fixed_ws);
+        if (e != cudaSuccess) return cuda_fail(e, "render_forward_noalloc: cudaGetSymbolAddress");
+        g_fixed_ptr[dev] = p;
+    }
+    *out = g_fixed_ptr[dev];
+    return NH_OK;
+}
+
+extern "C" nh_status render_forward_noalloc(const nh_field* f, const nh_geometry* g, const nh_ray_batch* b,
+                                            float* a_pred, void* stream) {
+    if (!f || !g || !b) return fail(NH_ERR_INVALID_ARG, "render_forward_noalloc: null handle or batch");
+    if (b->n_rays >= 0 && b->n_samples >= 1) {
+        const size_t need = ray_ws(nullptr, b->n_rays, b->n_samples).bytes;
+        if (need > kFixedWsBytes)
+            return fail(NH_ERR_SIZE_MISMATCH,
+                        "render_forward_noalloc: %d rays x %d samples need %zu bytes of scratch, the fixed block "
+                        "holds %zu; use render_forward with a caller workspace",
+                        b->n_rays, b->n_samples, need, kFixedWsBytes);
+    }
+    void* ws = nullptr;
+    const nh_status s = fixed_workspace(&ws);
+    if (s != NH_OK) return s;
+    return render_forward(f, g, b, a_pred, ws, kFixedWsBytes, stream);
 }

@@ -91,6 +91,7 @@ _SIGS = {
     "train_step_host": (_I, [_P, _P, _I, _I, _P, _P, _I, _P, _P, _SZ, _P]),
     "render_forward": (_I, [_P, _P, C.POINTER(RayBatch), _P, _P, _SZ, _P]),
     "render_backward": (_I, [_P, _P, C.POINTER(RayBatch), _P, _P, _SZ, _P]),
+    "render_forward_noalloc": (_I, [_P, _P, C.POINTER(RayBatch), _P, _P]),
     "optimizer_step": (_I, [_P, _P]),
     "fit_points_step": (_I, [_P, _I, _P, _P, _P, _P, _SZ, _P]),
     "fit_points_backward": (_I, [_P, _I, _P, _P, _P, _P, _SZ, _P]),
@@ -323,6 +324,15 @@ def render_forward(field, geom, view, pix, n_samples, a_pred, ws, stream=None):
     b = _batch(view, pix, None, n_samples)
     _check(load().render_forward(field.handle, geom.handle, C.byref(b), _ptr(a_pred), _ptr(ws),
                                  ws.numel() * 4, _stream(stream)), "render_forward")
+
+
+def render_forward_noalloc(field, geom, view, pix, n_samples, a_pred, stream=None):
+    """render_forward without a workspace argument, for callers that cannot allocate
+    device memory at call time; its scratch is a fixed 1 MiB block inside the library
+    (see include/nhcbct.h for the size limit and the rules on concurrent calls)."""
+    b = _batch(view, pix, None, n_samples)
+    _check(load().render_forward_noalloc(field.handle, geom.handle, C.byref(b), _ptr(a_pred), _stream(stream)),
+           "render_forward_noalloc")
 
 
 def render_backward(field, geom, view, pix, n_samples, dLdA, ws, stream=None):
