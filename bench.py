@@ -55,6 +55,13 @@ def parse_args():
     p.add_argument("--mixed", default="paper_bf16", help="mixed-precision workload measured beside ('' = skip)")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-psnr", action="store_true", help="skip the time-to-PSNR runs")
+    p.add_argument("--psnr-steps", type=int, default=3000, help="step cap of the time-to-PSNR runs")
+    p.add_argument("--experiment", default="", choices=["", "mci"])
+    p.add_argument("--mci-cases", type=int, default=8)
+    p.add_argument("--mci-heldout", type=int, default=8)
+    p.add_argument("--mci-recon-steps", type=int, default=1500)
+    p.add_argument("--mci-pretrain-steps", type=int, default=2000)
     p.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--seed", type=int, default=0)
     return p.parse_args()
@@ -209,6 +216,101 @@ def make_scan(nh, torch, w: S.Workload, seed: int, device):
     return geom, vol, a_meas, cands
 
 
+def device_batches(torch, w: S.Workload, cands, a_meas_all, n, seed, dev):
+    """n seeded batches (view, pix, a_meas) uploaded to the device, cycled forever."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        view, pix = S.pick_rays(rng, w.geometry.n_views, cands, w.n_rays)
+        out.append((view, torch.from_numpy(pix).to(dev),
+                    torch.from_numpy(a_meas_all[view][pix].astype(np.float32)).to(dev)))
+
+    def gen():
+        while True:
+            yield from out
+    return gen()
+
+
+def time_to_psnr(nh, torch, recon, w: S.Workload, seed, dev, targets=(25.0, 30.0, 35.0), max_steps=3000,
+                 eval_every=50, params=None, scan=None, ln_mlp=None):
+    """Trains workload w from its seeded phantom until the PSNR targets (or max_steps);
+    seconds are GPU time of the training steps only. ln_mlp: LN + MLP weights loaded
+    before training (Mapping Consistency Initialization)."""
+    geom, vol, a_meas_all, cands = scan if scan is not None else make_scan(nh, torch, w, seed, dev)
+    vol_gt = torch.from_numpy(vol.astype(np.float32).ravel()).to(dev)
+    rec = recon.Reconstruction(w.field, geom, params=params if params is not None else S.init_params(w.field, seed))
+    if ln_mlp is not None:
+        recon.transfer(ln_mlp, rec.field)
+    res = recon.train_to_psnr(rec, device_batches(torch, w, cands, a_meas_all, 500, seed + 5, dev),
+                              w.n_samples, vol_gt, targets=targets, eval_every=eval_every, max_steps=max_steps)
+    return res, rec
+
+
+def run_mci(args):
+    """Mapping Consistency Initialization (Sec. 2.1, 2.4): reconstruct pre-training
+    phantoms with the method itself, fit one LN + MLP to those reconstructions with
+    the voxel loss (Eq. 2), then train held-out phantoms from that LN + MLP or from
+    random initialisation and compare steps / seconds to 30 and 35 dB."""
+    import torch
+    from paper_2506_19742_gb300 import build as nhbuild
+    from paper_2506_19742_gb300 import nhcbct as nh
+    from paper_2506_19742_gb300 import recon
+    nhbuild.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    w = S.WORKLOADS[args.workload]
+    cfg = w.field
+    t0 = time.perf_counter()
+    vols, rec_psnr = [], []
+    for s in range(100, 100 + args.mci_cases):
+        res, rec = time_to_psnr(nh, torch, recon, w, s, dev, targets=(99.0,), max_steps=args.mci_recon_steps,
+                                eval_every=args.mci_recon_steps)
+        vols.append(rec.volume(w.vol_D))
+        rec_psnr.append(res["final_psnr"])
+        del rec
+    shared, pre_curve = recon.pretrain_mci(cfg, vols, steps=args.mci_pretrain_steps, points_per_step=65536,
+                                           seed=args.seed)
+    del vols
+    rows = []
+    for s in range(200, 200 + args.mci_heldout):
+        scan = make_scan(nh, torch, w, s, dev)
+        p0 = S.init_params(cfg, s)
+        rr, _ = time_to_psnr(nh, torch, recon, w, s, dev, targets=(25.0, 30.0, 35.0), max_steps=args.psnr_steps,
+                             params=p0, scan=scan)
+        rm, rec = time_to_psnr(nh, torch, recon, w, s, dev, targets=(25.0, 30.0, 35.0),
+                               max_steps=args.psnr_steps, params=p0, scan=scan, ln_mlp=shared)
+        rows.append({"seed": s, "random": {k: rr[k] for k in ("steps_to", "seconds_to", "final_psnr")},
+                     "mci": {k: rm[k] for k in ("steps_to", "seconds_to", "final_psnr")},
+                     "psnr_at": {"random": rr["curve"][:6], "mci": rm["curve"][:6]}})
+    # full-volume query throughput at 256^3 (M(x, y, z) of Eq. 2 on every voxel centre)
+    out = torch.empty(256 ** 3, device=dev)
+    for _ in range(3):
+        nh.query_volume(rec.field, 256, out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        nh.query_volume(rec.field, 256, out)
+    e1.record()
+    torch.cuda.synchronize()
+    q_ms = e0.elapsed_time(e1) / 10
+
+    def mean_steps(key, t):
+        v = [r[key]["steps_to"][t] for r in rows]
+        return None if any(x is None for x in v) else float(np.mean(v))
+
+    line = {"experiment": "mci", "workload": w.name, "precision": cfg.precision,
+            "pretrain_cases": args.mci_cases, "recon_steps": args.mci_recon_steps,
+            "pretrain_recon_psnr": rec_psnr, "pretrain_steps": args.mci_pretrain_steps,
+            "pretrain_points_per_step": 65536, "pretrain_loss": pre_curve,
+            "heldout": rows,
+            "mean_steps_to": {t: {"random": mean_steps("random", t), "mci": mean_steps("mci", t)}
+                              for t in ("25.0", "30.0", "35.0")},
+            "query_256_ms": q_ms, "query_points_per_s": 256 ** 3 / (q_ms / 1e3),
+            "wall_seconds": time.perf_counter() - t0}
+    print(json.dumps(line))
+
+
 def run_ours(args, rank: int, world: int, local_rank: int):
     import torch
     from paper_2506_19742_gb300 import build as nhbuild
@@ -350,6 +452,21 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                      "ms_per_step": ms_m / K, "speedup_vs_fp32": (samples_all / (ms_m / 1e3)) / value,
                      "launch_ms": {"forward+sum": round(tf, 4), "backward": round(tbk, 4), "adam": round(ta, 4)}}
 
+    # time to PSNR: FP32 and the mixed-precision workload on the same scan
+    psnr = None
+    if not args.no_psnr and rank == 0:
+        from paper_2506_19742_gb300 import recon
+        scan = (geom, vol, a_meas_all, cands)
+        r32, _ = time_to_psnr(nh, torch, recon, w, seed, dev, scan=scan, max_steps=args.psnr_steps)
+        psnr = {"fp32": {k: r32[k] for k in ("steps_to", "seconds_to", "final_psnr", "best_psnr", "steps")}}
+        if args.mixed and S.WORKLOADS[args.mixed].geometry == w.geometry:
+            rmx, _ = time_to_psnr(nh, torch, recon, S.WORKLOADS[args.mixed], seed, dev, scan=scan,
+                                  max_steps=args.psnr_steps)
+            psnr["mixed"] = {k: rmx[k] for k in ("steps_to", "seconds_to", "final_psnr", "best_psnr", "steps")}
+            s32, smx = r32["seconds_to"].get("30.0"), rmx["seconds_to"].get("30.0")
+            psnr["seconds_to_30dB_fp32_over_mixed"] = (s32 / smx) if (s32 and smx) else None
+            psnr["final_psnr_delta_db"] = round(rmx["final_psnr"] - r32["final_psnr"], 3)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, args.cpu_seconds, args.seed)
@@ -373,7 +490,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                          f"{4 * 4 * S.param_layout(f)['_total'][1] / 1e6:.0f} MB of parameter state",
                    "parallelism": f"replicas x{world}"},
         "clocks": clocks, "e2e": e2e, "gpu_launches": 5 * K, "roofline": roofline, "cpu_baseline": cpu,
-        "mixed": mixed, "final_loss": losses[-1] if losses else None,
+        "mixed": mixed, "psnr": psnr, "final_loss": losses[-1] if losses else None,
     }
     print(json.dumps(line))
 
@@ -412,7 +529,10 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
+    if args.experiment == "mci":
+        if rank == 0:
+            run_mci(args)
+    elif args.impl == "reference":
         run_reference(args, rank, world)
     else:
         run_ours(args, rank, world, local_rank)
