@@ -491,9 +491,15 @@ static uint32_t bwd_tmem_cols(const FieldArgs& fa) {
 // cap residency at two CTAs per SM; when one CTA takes all 512 TMEM columns the
 // request is padded so that only one CTA fits, and no tcgen05.alloc waits on a
 // resident CTA.
+// Per-warp scratch floats of the training kernels: the FFMA path's stage + dz tiles,
+// or the tensor-core path's two 16-bit tiles and row buffer.
+__host__ __device__ inline int bwd_warp_floats(int precision) {
+    return precision == NH_PREC_F32 ? warp_scratch_floats() : kMmaWarpFloats;
+}
+
 static size_t bwd_smem_bytes(const FieldArgs& fa) {
     const int ndp = (fa.n_dense + 3) & ~3;
-    size_t b = (size_t)(2 * ndp + kMaxD + kBwdWarps * warp_scratch_floats()) * sizeof(float);
+    size_t b = (size_t)(2 * ndp + kMaxD + kBwdWarps * bwd_warp_floats(fa.precision)) * sizeof(float);
     if (fa.precision != NH_PREC_F32) b += (size_t)fa.H * kMmaLayerElems * 2;
     if (512u / bwd_tmem_cols(fa) < 2u && b < 120 * 1024) b = 120 * 1024;
     return b;
@@ -514,8 +520,9 @@ __device__ __forceinline__ BwdCta bwd_begin(const FieldArgs& fa, float* smem, ui
     c.sp = smem;
     c.smask = c.sp + ndp;
     c.sg = c.smask + kMaxD;
-    c.wbuf = c.sg + ndp + warp * warp_scratch_floats();
-    uint16_t* sw = reinterpret_cast<uint16_t*>(c.sg + ndp + kBwdWarps * warp_scratch_floats());
+    const int wf = bwd_warp_floats(fa.precision);
+    c.wbuf = c.sg + ndp + warp * wf;
+    uint16_t* sw = reinterpret_cast<uint16_t*>(c.sg + ndp + kBwdWarps * wf);
     c.sw = sw;
     if (warp == 0) tmem_alloc(s_tmem, tcols);
     load_dense(fa, c.sp, c.smask);
