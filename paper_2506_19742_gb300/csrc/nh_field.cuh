@@ -38,6 +38,15 @@ struct DenseLayout {
     }
 };
 
+// Column permutation of the shared-memory weight-gradient accumulators of W_l
+// (l < H, 32 rows of IN = 16 or 32 columns): element (j, i) lives at
+// j IN + wswz(i, j, IN). It spreads every warp-wide accumulation of tensor-core
+// gradient fragments (8 rows x 4 column pairs) over 32 banks and keeps whole-row
+// accumulations conflict-free.
+__host__ __device__ __forceinline__ int wswz(int i, int j, int IN) {
+    return IN == 32 ? (i ^ ((j & 1) | ((j & 6) << 2))) : (i ^ (((j >> 1) & 1) | (((j >> 2) & 1) << 3)));
+}
+
 __device__ __forceinline__ void load_dense(const FieldArgs& fa, float* sp, float* smask) {
     const float* src = fa.params + fa.n_table;
     for (int k = threadIdx.x; k < fa.n_dense; k += blockDim.x) sp[k] = src[k];
@@ -284,7 +293,7 @@ __device__ __forceinline__ void warp_weight_grad(float* dzb, const float* stage,
             }
         }
 #pragma unroll
-        for (int j = 0; j < kW; j++) atomicAdd(sgW + j * IN + lane, acc[j]);
+        for (int j = 0; j < kW; j++) atomicAdd(sgW + j * IN + wswz(lane, j, IN), acc[j]);
     }
     float bsum = 0.f;
 #pragma unroll 8
@@ -556,9 +565,19 @@ __device__ __forceinline__ void bwd_end(const FieldArgs& fa, const BwdCta& c, ui
         tmem_fence_after_sync();
         tmem_dealloc(c.tbase, tcols);
     }
+    // flush: logical dense index k <- accumulator slot (W_l blocks are column-permuted)
+    const DenseLayout lay{fa.D, fa.H};
     float* gd = fa.grads + fa.n_table;
     for (int k = threadIdx.x; k < fa.n_dense; k += blockDim.x) {
-        const float v = c.sg[k];
+        int p = k;
+        for (int l = 0; l < fa.H; l++) {
+            const int IN = l == 0 ? fa.D : kW, o = k - lay.W(l);
+            if (o >= 0 && o < kW * IN) {
+                const int j = o / IN, i = o - j * IN;
+                p = lay.W(l) + j * IN + wswz(i, j, IN);
+            }
+        }
+        const float v = c.sg[p];
         if (v != 0.f) atomicAdd(gd + k, v);
     }
 }

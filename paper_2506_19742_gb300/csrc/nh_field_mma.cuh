@@ -243,7 +243,7 @@ __device__ __forceinline__ void mlp_backward_mma(const DenseLayout& lay, const u
 #pragma unroll
                         for (int c = 0; c < 4; c++) {
                             const int j = 16 * mj + g + 8 * (c >> 1), i = 8 * nt + 2 * t + (c & 1);
-                            atomicAdd(gW + j * IN + i, dW[nt][c]);
+                            atomicAdd(gW + j * IN + wswz(i, j, IN), dW[nt][c]);
                         }
                     }
                 }
