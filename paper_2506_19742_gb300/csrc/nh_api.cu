@@ -372,6 +372,7 @@ struct RayWs {
     float* a_pred;
     float* dLdA;
     float* loss;
+    float* loss_part;   // per-CTA loss partials of the fused step
     size_t bytes;
 };
 
@@ -386,6 +387,7 @@ static RayWs ray_ws(void* base, int R, int N) {
     w.a_pred = (float*)(b + o); o = align_up(o + sizeof(float) * (size_t)R, 256);
     w.dLdA = (float*)(b + o); o = align_up(o + sizeof(float) * (size_t)R, 256);
     w.loss = (float*)(b + o); o = align_up(o + sizeof(float) * 4, 256);
+    w.loss_part = (float*)(b + o); o = align_up(o + sizeof(float) * kTrainParts, 256);
     w.bytes = o;
     return w;
 }
@@ -428,10 +430,15 @@ static nh_status run_train(nh_field* f, const nh_geometry* g, int view, int R, c
         if (loss_dev) NH_CUDA(cudaMemsetAsync(loss_dev, 0, sizeof(float), st), "train_step");
         return NH_OK;
     }
-    NH_CUDA(launch_ray_forward(f->fa, va, pix, R, N, w.ray_part, st), "train_step forward");
-    NH_CUDA(launch_ray_loss(w.ray_part, R, C, a_meas, f->desc.loss, w.a_pred, w.dLdA, loss_dev, f->fa.state,
-                            true, st), "train_step loss");
-    NH_CUDA(launch_ray_backward(f->fa, va, pix, R, N, w.dLdA, st), "train_step backward");
+    if (C <= 8) {   // whole rays fit a CTA: one fused forward + loss + backward kernel
+        NH_CUDA(launch_ray_train(f->fa, va, pix, a_meas, R, N, f->desc.loss, w.loss_part, loss_dev, st),
+                "train_step fused");
+    } else {
+        NH_CUDA(launch_ray_forward(f->fa, va, pix, R, N, w.ray_part, st), "train_step forward");
+        NH_CUDA(launch_ray_loss(w.ray_part, R, C, a_meas, f->desc.loss, w.a_pred, w.dLdA, loss_dev, f->fa.state,
+                                true, st), "train_step loss");
+        NH_CUDA(launch_ray_backward(f->fa, va, pix, R, N, w.dLdA, st), "train_step backward");
+    }
     NH_CUDA(launch_adam(f->fa, f->buf.params, f->buf.grads, f->buf.adam_m, f->buf.adam_v,
                         (int64_t)align_up(f->sizes.n_params, 4), f->desc.lr, f->desc.beta1, f->desc.beta2,
                         f->desc.adam_eps, f->desc.growth_interval, st), "train_step adam");

@@ -357,55 +357,70 @@ __device__ __forceinline__ void nhe_backward_scatter(const FieldArgs& fa, const 
     scatter_point<D / 2>(fa, x, row, lane);
 }
 
-// Forward with activations kept in TMEM, then the full backward of one sample per
-// lane. dmu_of(mu) gives dL/dmu (already multiplied by the loss scale); inactive
-// lanes use dmu = 0 and skip the scatter. All 32 lanes must call it together.
-template <int D, typename TT, class DmuFn>
-__device__ __forceinline__ float sample_fwd_bwd(const FieldArgs& fa, const float* sp, const float* smask,
-                                                float* sg, float* wbuf, uint32_t tslot0, const float x[3],
-                                                bool active, int lane, DmuFn dmu_of) {
+// State of one training sample carried from the forward half to the backward half
+// (everything else is in tensor memory): FFMA path.
+template <int D>
+struct FfmaCarry {
+    float rstd[D / 2];
+    float a[kW];   // a_H, input of the output layer
+    float mu;
+};
+
+// Forward of one sample per lane with activations kept in TMEM (slot 0: hhat, slot
+// k: a_k); a_H stays in the carry.
+template <int D, typename TT>
+__device__ __forceinline__ void ffma_forward(const FieldArgs& fa, const float* sp, const float* smask,
+                                             uint32_t tslot0, const float x[3], FfmaCarry<D>& s) {
     constexpr int L = D / 2;
     const DenseLayout lay{D, fa.H};
     const int H = fa.H;
-    float* stage = wbuf;
-    float* dzb = wbuf + kStage;
-
-    float rstd[D / 2];
-    float a[kW];
     {
         float h[D], hhat[D], y[D];
         encode_point<L, TT>(fa, table_base<TT>(fa), x, h);
-        nhe_forward<D>(fa, sp, smask, h, hhat, rstd, y);
+        nhe_forward<D>(fa, sp, smask, h, hhat, s.rstd, y);
         tmem_st(tslot0, hhat);
         float z[kW];
         linear_fwd<D, kW>(sp + lay.W(0), sp + lay.b(0), y, z);
 #pragma unroll
-        for (int j = 0; j < kW; j++) a[j] = fmaxf(z[j], 0.f);
+        for (int j = 0; j < kW; j++) s.a[j] = fmaxf(z[j], 0.f);
     }
 #pragma unroll 1
     for (int k = 1; k < H; k++) {
-        tmem_st(tslot0 + 32 * k, a);
+        tmem_st(tslot0 + 32 * k, s.a);
         float z[kW];
-        linear_fwd<kW, kW>(sp + lay.W(k), sp + lay.b(k), a, z);
+        linear_fwd<kW, kW>(sp + lay.W(k), sp + lay.b(k), s.a, z);
 #pragma unroll
-        for (int j = 0; j < kW; j++) a[j] = fmaxf(z[j], 0.f);
+        for (int j = 0; j < kW; j++) s.a[j] = fmaxf(z[j], 0.f);
     }
     const float* wo = sp + lay.W(H);
     float zo = sp[lay.b(H)];
 #pragma unroll
-    for (int j = 0; j < kW; j++) zo = fmaf(wo[j], a[j], zo);
-    const float mu = 1.f / (1.f + expf(-zo));
-    const float dmu = active ? dmu_of(mu) : 0.f;
+    for (int j = 0; j < kW; j++) zo = fmaf(wo[j], s.a[j], zo);
+    s.mu = 1.f / (1.f + expf(-zo));
+}
+
+// Backward of one sample per lane given dL/dmu (already multiplied by the loss
+// scale; 0 for lanes without a sample). All 32 lanes must call it together.
+template <int D, typename TT>
+__device__ __forceinline__ void ffma_backward(const FieldArgs& fa, const float* sp, const float* smask, float* sg,
+                                              float* wbuf, uint32_t tslot0, const float x[3], bool active, int lane,
+                                              const FfmaCarry<D>& s, float dmu) {
+    const DenseLayout lay{D, fa.H};
+    const int H = fa.H;
+    float* stage = wbuf;
+    float* dzb = wbuf + kStage;
+    const float mu = s.mu;
     const float dzo = dmu * mu * (1.f - mu);
+    const float* wo = sp + lay.W(H);
 
     // output layer: dW_H[0][i] = sum_s dzo[s] a_H[s][i], db_H = sum_s dzo[s]
-    stage_row<kW>(stage, lane, a);
+    stage_row<kW>(stage, lane, s.a);
     dzb[lane] = dzo;
     __syncwarp();
     {
         float acc = 0.f;
 #pragma unroll 8
-        for (int s = 0; s < 32; s++) acc = fmaf(dzb[s], stage[s * (kW + 1) + lane], acc);
+        for (int t = 0; t < 32; t++) acc = fmaf(dzb[t], stage[t * (kW + 1) + lane], acc);
         atomicAdd(sg + lay.W(H) + lane, acc);
         const float bs = warp_sum(dzo);
         if (lane == 0) atomicAdd(sg + lay.b(H), bs);
@@ -413,7 +428,7 @@ __device__ __forceinline__ float sample_fwd_bwd(const FieldArgs& fa, const float
     __syncwarp();
     float dz[kW];
 #pragma unroll
-    for (int j = 0; j < kW; j++) dz[j] = (a[j] > 0.f) ? wo[j] * dzo : 0.f;
+    for (int j = 0; j < kW; j++) dz[j] = (s.a[j] > 0.f) ? wo[j] * dzo : 0.f;
 
     // hidden layers k = H-1 .. 1: input a_k from TMEM
 #pragma unroll 1
@@ -446,42 +461,72 @@ __device__ __forceinline__ float sample_fwd_bwd(const FieldArgs& fa, const float
     }
     float dh[D];
     linear_bwd_data<D, kW>(sp + lay.W(0), dz, dh);   // dh <- dL/dy
-    nhe_backward_scatter<D>(fa, sp, smask, sg, dzb, hhat, rstd, dh, x, active, lane);
-    return mu;
+    nhe_backward_scatter<D>(fa, sp, smask, sg, dzb, hhat, s.rstd, dh, x, active, lane);
 }
 
-// Mixed-precision counterpart of sample_fwd_bwd: the MLP of the warp's 32 samples
-// runs on tensor cores (nh_field_mma.cuh); encoding, normalization, LN backward and
-// the scatter are the per-sample float32 code. All 32 lanes must call it together.
+// Forward then backward of one sample per lane; dmu_of(mu) gives dL/dmu.
 template <int D, typename TT, class DmuFn>
-__device__ __forceinline__ float sample_fwd_bwd_mma(const FieldArgs& fa, const float* sp, const uint16_t* sw,
-                                                    const float* smask, float* sg, float* wbuf, uint32_t tslot0,
-                                                    const float x[3], bool active, int lane, DmuFn dmu_of) {
+__device__ __forceinline__ float sample_fwd_bwd(const FieldArgs& fa, const float* sp, const float* smask,
+                                                float* sg, float* wbuf, uint32_t tslot0, const float x[3],
+                                                bool active, int lane, DmuFn dmu_of) {
+    FfmaCarry<D> s;
+    ffma_forward<D, TT>(fa, sp, smask, tslot0, x, s);
+    ffma_backward<D, TT>(fa, sp, smask, sg, wbuf, tslot0, x, active, lane, s, active ? dmu_of(s.mu) : 0.f);
+    return s.mu;
+}
+
+// Tensor-core path: the MLP of the warp's 32 samples runs on tensor cores
+// (nh_field_mma.cuh); encoding, normalization, LN backward and the scatter are the
+// per-sample float32 code. All 32 lanes must call these together.
+template <int D>
+struct MmaCarry {
+    float rstd[D / 2];
+    float C[2][4][4];   // last hidden layer pre-activations (fragments)
+    float mu;
+};
+
+template <int D, typename TT>
+__device__ __forceinline__ void mma_forward(const FieldArgs& fa, const float* sp, const uint16_t* sw,
+                                            const float* smask, float* wbuf, uint32_t tslot0, const float x[3],
+                                            int lane, MmaCarry<D>& s) {
     constexpr int L = D / 2;
+    const DenseLayout lay{D, fa.H};
+    uint16_t* tile = reinterpret_cast<uint16_t*>(wbuf);
+    float* rowbuf = reinterpret_cast<float*>(tile + 2 * kTile16);
+    float h[D], hhat[D], y[D];
+    encode_point<L, TT>(fa, table_base<TT>(fa), x, h);
+    nhe_forward<D>(fa, sp, smask, h, hhat, s.rstd, y);
+    tmem_st(tslot0, hhat);
+    s.mu = mlp_mu_mma<TT, D, true>(lay, sp, sw, y, tile, rowbuf, lane, tslot0 + 32, s.C);
+}
+
+template <int D, typename TT>
+__device__ __forceinline__ void mma_backward(const FieldArgs& fa, const float* sp, const uint16_t* sw,
+                                             const float* smask, float* sg, float* wbuf, uint32_t tslot0,
+                                             const float x[3], bool active, int lane, const MmaCarry<D>& s,
+                                             float dmu) {
     const DenseLayout lay{D, fa.H};
     uint16_t* tile = reinterpret_cast<uint16_t*>(wbuf);
     uint16_t* dztile = tile + kTile16;
     float* rowbuf = reinterpret_cast<float*>(dztile + kTile16);
-    float rstd[D / 2];
-    float C[2][4][4];
-    float mu;
-    {
-        float h[D], hhat[D], y[D];
-        encode_point<L, TT>(fa, table_base<TT>(fa), x, h);
-        nhe_forward<D>(fa, sp, smask, h, hhat, rstd, y);
-        tmem_st(tslot0, hhat);
-        mu = mlp_mu_mma<TT, D, true>(lay, sp, sw, y, tile, rowbuf, lane, tslot0 + 32, C);
-    }
-    const float dmu = active ? dmu_of(mu) : 0.f;
-    const float dzo = dmu * mu * (1.f - mu);
+    const float dzo = dmu * s.mu * (1.f - s.mu);
     float dz[2][4][4];
-    out_layer_backward_mma<4>(lay, sp, sg, rowbuf, lane, dzo, C, dz);
+    out_layer_backward_mma<4>(lay, sp, sg, rowbuf, lane, dzo, s.C, dz);
     float dh[D];
     mlp_backward_mma<TT, D>(lay, sw, sg, tile, dztile, lane, tslot0 + 32, dz, dh);
     float hhat[D];
     tmem_ld(tslot0, hhat);
-    nhe_backward_scatter<D>(fa, sp, smask, sg, wbuf, hhat, rstd, dh, x, active, lane);
-    return mu;
+    nhe_backward_scatter<D>(fa, sp, smask, sg, wbuf, hhat, s.rstd, dh, x, active, lane);
+}
+
+template <int D, typename TT, class DmuFn>
+__device__ __forceinline__ float sample_fwd_bwd_mma(const FieldArgs& fa, const float* sp, const uint16_t* sw,
+                                                    const float* smask, float* sg, float* wbuf, uint32_t tslot0,
+                                                    const float x[3], bool active, int lane, DmuFn dmu_of) {
+    MmaCarry<D> s;
+    mma_forward<D, TT>(fa, sp, sw, smask, wbuf, tslot0, x, lane, s);
+    mma_backward<D, TT>(fa, sp, sw, smask, sg, wbuf, tslot0, x, active, lane, s, active ? dmu_of(s.mu) : 0.f);
+    return s.mu;
 }
 
 // TMEM columns of one thread: FFMA path 32 H (hhat, a_1 .. a_{H-1}); tensor-core
@@ -605,6 +650,112 @@ k_ray_backward(FieldArgs fa, ViewArgs va, const int32_t* __restrict__ pix, int R
         train_sample<D, TT>(fa, cta, x, active, lane, [gr](float) { return gr; });
     }
     bwd_end(fa, cta, tcols);
+}
+
+// ============================================================================ fused step
+// One training step for batches whose rays fit a CTA (at most kBwdWarps chunks of
+// 32 samples per ray): a CTA takes rpr whole rays at a time, warp w computing chunk
+// w % C of ray w / C. Each warp runs the forward of its samples with activations in
+// tensor memory; the CTA sums each ray's chunks in order into A_r (Eq. 1), forms the
+// loss term and dL/dA_r (MSE or L1, Eq. 3) in shared memory, and every warp carries
+// on with the backward of the same samples. Ray-tile losses are accumulated in ray
+// order per CTA; k_train_loss adds the CTA partials in order.
+template <int D, typename TT>
+struct TrainCarry {
+    using type = FfmaCarry<D>;
+};
+
+template <int D>
+struct TrainCarry<D, __nv_bfloat16> {
+    using type = MmaCarry<D>;
+};
+
+template <int D>
+struct TrainCarry<D, __half> {
+    using type = MmaCarry<D>;
+};
+
+template <int D, typename TT>
+__global__ void __launch_bounds__(kBwdWarps * 32, 2)
+k_ray_train(FieldArgs fa, ViewArgs va, const int32_t* __restrict__ pix, const float* __restrict__ a_meas, int R,
+            int N, int C, int rpr, int loss_kind, float* __restrict__ loss_part, uint32_t tcols) {
+    extern __shared__ __align__(16) float smem[];
+    __shared__ uint32_t s_tmem;
+    __shared__ float s_part[kBwdWarps];
+    __shared__ float s_g[kBwdWarps];
+    __shared__ float s_lr[kBwdWarps];
+    __shared__ float s_loss;
+    const BwdCta cta = bwd_begin<TT>(fa, smem, &s_tmem, tcols);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rl = warp / C, c = warp - rl * C;
+    const float scale = fa.state->loss_scale;
+    const float invR = 1.f / (float)R;
+    if (threadIdx.x == 0) s_loss = 0.f;
+    const int ngroups = (R + rpr - 1) / rpr;
+    for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+        const int r = grp * rpr + rl;
+        RayGeo g{};
+        g.hit = false;
+        if (r < R) g = ray_setup(va, pix[r], N);
+        const bool work = g.hit;                       // uniform over the warp
+        const int i = c * 32 + lane;
+        const bool active = work && i < N;
+        float x[3] = {0.f, 0.f, 0.f};
+        typename TrainCarry<D, TT>::type st;
+        st.mu = 0.f;
+        if (work) {
+            sample_position(g, i < N ? i : N - 1, x);
+            if constexpr (kMmaPath<TT>)
+                mma_forward<D, TT>(fa, cta.sp, cta.sw, cta.smask, cta.wbuf, cta.tslot0, x, lane, st);
+            else
+                ffma_forward<D, TT>(fa, cta.sp, cta.smask, cta.tslot0, x, st);
+        }
+        const float part = warp_sum(active ? st.mu : 0.f) * (work ? g.delta : 0.f);
+        if (lane == 0) s_part[warp] = part;
+        __syncthreads();
+        if ((int)threadIdx.x < rpr) {
+            const int rr = grp * rpr + threadIdx.x;
+            float gr = 0.f, l = 0.f;
+            if (rr < R) {
+                float A = 0.f;
+                for (int cc = 0; cc < C; cc++) A += s_part[threadIdx.x * C + cc];
+                const float res = A - a_meas[rr];
+                if (loss_kind == NH_LOSS_MSE) {
+                    l = res * res;
+                    gr = 2.f * res * invR;
+                } else {
+                    l = fabsf(res);
+                    gr = (res > 0.f ? 1.f : (res < 0.f ? -1.f : 0.f)) * invR;
+                }
+            }
+            s_g[threadIdx.x] = gr * scale;
+            s_lr[threadIdx.x] = l;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int t = 0; t < rpr && grp * rpr + t < R; t++) s_loss += s_lr[t];
+        if (work) {
+            const float dmu = active ? s_g[rl] * g.delta : 0.f;
+            if constexpr (kMmaPath<TT>)
+                mma_backward<D, TT>(fa, cta.sp, cta.sw, cta.smask, cta.sg, cta.wbuf, cta.tslot0, x, active, lane, st,
+                                    dmu);
+            else
+                ffma_backward<D, TT>(fa, cta.sp, cta.smask, cta.sg, cta.wbuf, cta.tslot0, x, active, lane, st, dmu);
+        }
+    }
+    bwd_end(fa, cta, tcols);
+    if (threadIdx.x == 0) loss_part[blockIdx.x] = s_loss;
+}
+
+// loss = (sum of CTA partials in order) / R.
+static __global__ void k_train_loss(const float* __restrict__ part, int n_part, int R, float* loss_out,
+                                    DeviceState* state) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    float s = 0.f;
+    for (int k = 0; k < n_part; k++) s += part[k];
+    const float loss = s / (float)R;
+    if (loss_out) *loss_out = loss;
+    if (!isfinite(loss)) atomicOr(&state->flags, NH_FLAG_NONFINITE);
 }
 
 // ============================================================================ points
@@ -766,7 +917,7 @@ static size_t dense_smem(const FieldArgs& fa) {
 // shared memory, and never more than TMEM holds (512 columns per SM), so every
 // CTA's tcgen05.alloc is satisfied without waiting for another CTA to finish.
 template <typename K>
-static long long train_grid(K kernel, size_t smem, uint32_t tcols, long long need);
+static long long train_grid(K kernel, size_t smem, uint32_t tcols, long long need, int threads = kBwdWarps * 32);
 
 // Opts the kernel into `bytes` of dynamic shared memory and the largest shared
 // memory carveout, so that occupancy queries and launches see the same capacity.
@@ -813,8 +964,8 @@ static int resident_ctas(K kernel, size_t dyn_smem, int threads) {
 }
 
 template <typename K>
-static long long train_grid(K kernel, size_t smem, uint32_t tcols, long long need) {
-    const int occ = resident_ctas(kernel, smem, kBwdWarps * 32);
+static long long train_grid(K kernel, size_t smem, uint32_t tcols, long long need, int threads) {
+    const int occ = resident_ctas(kernel, smem, threads);
     const int by_tmem = (int)(512u / tcols);
     int per_sm = occ < by_tmem ? occ : by_tmem;
     if (per_sm < 1) per_sm = 1;
@@ -928,7 +1079,36 @@ cudaError_t launch_query_volume_tt(const FieldArgs& fa, int D, float* out, cudaS
     return cudaGetLastError();
 }
 
+// Fused training step (k_ray_train) when a ray has at most kBwdWarps chunks of 32
+// samples; returns cudaErrorNotSupported otherwise (the caller then runs forward,
+// loss and backward as separate kernels). loss_part: >= 4096 floats of workspace.
+template <typename TT>
+cudaError_t launch_ray_train_tt(const FieldArgs& fa, const ViewArgs& va, const int32_t* pix, const float* a_meas,
+                                int R, int N, int loss_kind, float* loss_part, float* loss_out, cudaStream_t st) {
+    const int C = (N + 31) / 32;
+    if (C > kBwdWarps || R <= 0) return cudaErrorNotSupported;
+    const int rpr = kBwdWarps / C;
+    const int threads = rpr * C * 32;
+    const long long ngroups = ((long long)R + rpr - 1) / rpr;
+    const size_t sm = bwd_smem_bytes(fa);
+    const uint32_t tcols = bwd_tmem_cols(fa);
+    NH_DISPATCH_D(fa, {
+        auto k = k_ray_train<D_, TT>;
+        cudaError_t e = set_smem(k, sm);
+        if (e != cudaSuccess) return e;
+        long long blocks = train_grid(k, sm, tcols, ngroups, threads);
+        if (blocks > 4096) blocks = 4096;
+        k<<<(unsigned)blocks, threads, sm, st>>>(fa, va, pix, a_meas, R, N, C, rpr, loss_kind, loss_part, tcols);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_train_loss<<<1, 32, 0, st>>>(loss_part, (int)blocks, R, loss_out, fa.state);
+    });
+    return cudaGetLastError();
+}
+
 #define NH_INSTANTIATE_FIELD(TT)                                                                            \
+    template cudaError_t launch_ray_train_tt<TT>(const FieldArgs&, const ViewArgs&, const int32_t*, const float*, \
+                                                 int, int, int, float*, float*, cudaStream_t);              \
     template cudaError_t launch_ray_forward_tt<TT>(const FieldArgs&, const ViewArgs&, const int32_t*, int, int, \
                                                    float*, cudaStream_t);                                   \
     template cudaError_t launch_ray_backward_tt<TT>(const FieldArgs&, const ViewArgs&, const int32_t*, int,   \

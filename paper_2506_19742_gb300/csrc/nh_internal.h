@@ -63,6 +63,11 @@ cudaError_t launch_ray_loss(const float* ray_part, int R, int C, const float* a_
                             bool scale_by_loss_scale, cudaStream_t st);
 cudaError_t launch_ray_backward(const FieldArgs& fa, const ViewArgs& va, const int32_t* pix, int R,
                                 int N, const float* dLdA, cudaStream_t st);
+// Fused forward + loss + backward (rays of at most 8 chunks of 32 samples);
+// cudaErrorNotSupported for longer rays. loss_part: >= kTrainParts floats.
+constexpr int kTrainParts = 4096;
+cudaError_t launch_ray_train(const FieldArgs& fa, const ViewArgs& va, const int32_t* pix, const float* a_meas,
+                             int R, int N, int loss_kind, float* loss_part, float* loss_out, cudaStream_t st);
 // query (mu_gt == null) or MCI fit step (loss written to loss_out, CTA partials in loss_part)
 cudaError_t launch_points(const FieldArgs& fa, int n, const float* xyz, const float* mu_gt,
                           float* mu_out, float* loss_part, int n_part, float* loss_out,

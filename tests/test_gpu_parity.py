@@ -167,6 +167,38 @@ def test_train_step_loss_and_gradients_match_oracle(lib, case, loss):
     assert step == 1 and flags == 0
 
 
+@pytest.mark.parametrize("precision", [S.PREC_F32, S.PREC_BF16])
+@pytest.mark.parametrize("N", [64, 192, 300])
+def test_train_step_fused_and_split_paths_match_oracle(lib, precision, N):
+    """train_step runs one fused forward+loss+backward kernel when a ray has at most
+    8 chunks of 32 samples (N <= 256) and separate kernels otherwise (N = 300): both
+    give the oracle's loss, and one step's parameter update agrees with the update the
+    oracle's gradient gives."""
+    cfg = field_cfg(n_levels=16, hidden_layers=4, log2_T=12, max_res=256, precision=precision,
+                    loss_scale_init=1.0)
+    flat = S.init_params(cfg, 40, table_scale=0.5).astype(np.float32)
+    field = lib.Field(cfg, params=flat)
+    geom = lib.Geometry.from_config(GEOM)
+    og = oracle_geom(GEOM)
+    pix = batch(GEOM, 2, 190, seed=N, n_miss=2)
+    a_meas = np.random.default_rng(N).uniform(0, 0.8, size=len(pix)).astype(np.float32)
+    ref_flat = rounded_tables(flat, cfg, precision).astype(np.float64)
+    A, cache = oracle.render_forward(ref_flat, cfg, og, 2, pix, N)
+    ref_loss, dLdA = oracle.loss_and_grad(A, a_meas, S.LOSS_MSE)
+    ws = lib.workspace(lib.step_workspace_bytes(field, len(pix), N))
+    loss_t = torch.zeros(1, device="cuda")
+    lib.train_step(field, geom, 2, _t(pix), _t(a_meas), N, loss_t, ws)
+    tol_f = 1e-5 if precision == S.PREC_F32 else MIXED_TOL[precision][0]
+    assert abs(_np(loss_t)[0] - ref_loss) <= 2 * tol_f * ref_loss
+    # first Adam step: p - lr * g / (|g| + eps); compare where the oracle's |g| is not tiny
+    g = oracle.render_backward(cache, dLdA, cfg)
+    step = _np(field.flat_params()).astype(np.float64) - flat.astype(np.float64)
+    big = np.abs(g) > 1e-3 * np.abs(g).max()
+    expect = -cfg.lr * g / (np.abs(g) + cfg.adam_eps)
+    agree = np.mean(np.abs(step[big] - expect[big]) < 0.1 * cfg.lr)
+    assert agree > (0.999 if precision == S.PREC_F32 else 0.97), agree
+
+
 def test_autograd_function_matches_oracle(lib):
     cfg = field_cfg(n_levels=16, hidden_layers=4, log2_T=10, max_res=300)
     flat = S.init_params(cfg, 3, table_scale=0.5).astype(np.float32)
