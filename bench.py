@@ -381,7 +381,6 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
     # per-kernel durations (CUDA events on the launching stream) for the roofline
     stream = torch.cuda.current_stream()
-    a_pred = torch.empty(R, device=dev)
     nk = min(K, 20)
 
     def timed(fn):
@@ -393,31 +392,37 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         torch.cuda.synchronize()
         return float(np.mean([a.elapsed_time(b) for a, b in evs]))
 
-    dLdA = torch.full((R,), 1e-3, device=dev)
+
+
+    fused = (N + 31) // 32 <= 8
+    loss_k = torch.zeros(1, device=dev)
 
     def kernel_ms(fld, wsp):
-        t_f = timed(lambda i: nh.render_forward(fld, geom, dev_batches[W + i][0], dev_batches[W + i][1], N,
-                                                a_pred, wsp))
-        t_b = timed(lambda i: nh.render_backward(fld, geom, dev_batches[W + i][0], dev_batches[W + i][1], N,
-                                                 dLdA, wsp))
+        """Device time of the step's parts: forward + loss + backward (one fused kernel
+        when rays fit a CTA, else three), then Adam; each timed alone with CUDA events."""
+        t_acc = timed(lambda i: nh.accumulate_step(fld, geom, dev_batches[W + i][0], dev_batches[W + i][1],
+                                                   dev_batches[W + i][2], N, loss_k, wsp))
         info = nh.launch_info()
         t_a = timed(lambda i: nh.optimizer_step(fld))
-        return t_f, t_b, t_a, info
+        return t_acc, t_a, info
 
-    t_fwd, t_bwd, t_adam, launch = kernel_ms(field, ws)
+    t_acc, t_adam, launch = kernel_ms(field, ws)
     peaks, peak_kind = read_peaks()
     tb = 4 if w.field.precision == S.PREC_F32 else 2
     L, F = w.field.n_levels, w.field.n_feat
-    bytes_per_sample = L * 8 * F * tb + L * 8 * F * 4     # gather + scatter payload
-    achieved = bytes_per_sample * R * N / (t_bwd / 1e3) / 1e9
+    # algorithmic bytes per ray-sample: one trilinear gather (8 corners x F features per
+    # level) and one scatter of the same payload as float32 into the gradient tables;
+    # the split path re-gathers in its backward
+    bytes_per_sample = L * 8 * F * tb * (1 if fused else 2) + L * 8 * F * 4
+    achieved = bytes_per_sample * R * N / (t_acc / 1e3) / 1e9
     peak = peaks["hbm_gbs"]
-    roofline = {"kernel": "k_ray_backward", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+    kname = "ray_train" if fused else "ray_backward"
+    roofline = {"kernel": "k_" + kname, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": profiled_traffic("ray_backward", w.name),
+                "traffic": profiled_traffic(kname, w.name),
                 "peak_source": f"{peak_kind} hbm_gbs",
                 "bytes_per_sample": bytes_per_sample, "units_per_launch": R * N,
-                "launch_ms": {"forward+sum": round(t_fwd, 4), "backward": round(t_bwd, 4),
-                              "adam": round(t_adam, 4)},
+                "launch_ms": {"forward+loss+backward": round(t_acc, 4), "adam": round(t_adam, 4)},
                 "launch": launch}
 
     # end to end through the host-buffer entry point (pinned host in, loss out)
@@ -447,10 +452,10 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         if wm.n_rays == R and wm.n_samples == N and wm.geometry == w.geometry:
             field_m, ws_m, ms_m = measure(wm)
             ms_m = allmax(ms_m)
-            tf, tbk, ta, _ = kernel_ms(field_m, ws_m)
+            tacc, ta, _ = kernel_ms(field_m, ws_m)
             mixed = {"workload": wm.name, "value": samples_all / (ms_m / 1e3), "unit": UNIT,
                      "ms_per_step": ms_m / K, "speedup_vs_fp32": (samples_all / (ms_m / 1e3)) / value,
-                     "launch_ms": {"forward+sum": round(tf, 4), "backward": round(tbk, 4), "adam": round(ta, 4)}}
+                     "launch_ms": {"forward+loss+backward": round(tacc, 4), "adam": round(ta, 4)}}
 
     # time to PSNR: FP32 and the mixed-precision workload on the same scan
     psnr = None
@@ -489,7 +494,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                    "l2": "working set larger than L2: each step's Adam streams "
                          f"{4 * 4 * S.param_layout(f)['_total'][1] / 1e6:.0f} MB of parameter state",
                    "parallelism": f"replicas x{world}"},
-        "clocks": clocks, "e2e": e2e, "gpu_launches": 5 * K, "roofline": roofline, "cpu_baseline": cpu,
+        "clocks": clocks, "e2e": e2e, "gpu_launches": (4 if fused else 5) * K, "roofline": roofline, "cpu_baseline": cpu,
         "mixed": mixed, "psnr": psnr, "final_loss": losses[-1] if losses else None,
     }
     print(json.dumps(line))

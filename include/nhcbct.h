@@ -189,6 +189,12 @@ nh_status step_workspace_bytes(const nh_field* f, int32_t n_rays, int32_t n_samp
  * loss_dev[0] (device float), backward into grads, Adam (Sec. 3.1). */
 nh_status train_step(nh_field* f, const nh_geometry* g, const nh_ray_batch* b, float* loss_dev,
                      void* ws, size_t ws_bytes, void* stream);
+/* train_step without the optimizer: forward, loss (written to loss_dev[0]) and
+ * backward, ACCUMULATING into grads, so that several batches can be accumulated
+ * before one optimizer_step. When every ray has at most 8 chunks of 32 samples
+ * (n_samples <= 256) this is one fused kernel per call. */
+nh_status accumulate_step(nh_field* f, const nh_geometry* g, const nh_ray_batch* b, float* loss_dev,
+                          void* ws, size_t ws_bytes, void* stream);
 /* The same step from HOST arrays (pinned memory for asynchrony): pix_host and
  * a_meas_host are copied into the workspace, and the loss is copied back to
  * loss_host, valid once the stream has synchronized. */

@@ -422,14 +422,11 @@ static nh_status check_batch(const nh_field* f, const nh_geometry* g, const nh_r
     return NH_OK;
 }
 
-static nh_status run_train(nh_field* f, const nh_geometry* g, int view, int R, const int32_t* pix,
-                           const float* a_meas, int N, float* loss_dev, const RayWs& w, cudaStream_t st) {
+// Forward, loss and backward of one batch, accumulating into grads (R > 0).
+static nh_status run_accumulate(nh_field* f, const nh_geometry* g, int view, int R, const int32_t* pix,
+                                const float* a_meas, int N, float* loss_dev, const RayWs& w, cudaStream_t st) {
     const ViewArgs va = view_args(g, view);
     const int C = (N + 31) / 32;
-    if (R == 0) {   // empty batch: loss 0, no update
-        if (loss_dev) NH_CUDA(cudaMemsetAsync(loss_dev, 0, sizeof(float), st), "train_step");
-        return NH_OK;
-    }
     if (C <= 8) {   // whole rays fit a CTA: one fused forward + loss + backward kernel
         NH_CUDA(launch_ray_train(f->fa, va, pix, a_meas, R, N, f->desc.loss, w.loss_part, loss_dev, st),
                 "train_step fused");
@@ -439,10 +436,33 @@ static nh_status run_train(nh_field* f, const nh_geometry* g, int view, int R, c
                                 true, st), "train_step loss");
         NH_CUDA(launch_ray_backward(f->fa, va, pix, R, N, w.dLdA, st), "train_step backward");
     }
+    return NH_OK;
+}
+
+static nh_status run_train(nh_field* f, const nh_geometry* g, int view, int R, const int32_t* pix,
+                           const float* a_meas, int N, float* loss_dev, const RayWs& w, cudaStream_t st) {
+    if (R == 0) {   // empty batch: loss 0, no update
+        if (loss_dev) NH_CUDA(cudaMemsetAsync(loss_dev, 0, sizeof(float), st), "train_step");
+        return NH_OK;
+    }
+    const nh_status s = run_accumulate(f, g, view, R, pix, a_meas, N, loss_dev, w, st);
+    if (s != NH_OK) return s;
     NH_CUDA(launch_adam(f->fa, f->buf.params, f->buf.grads, f->buf.adam_m, f->buf.adam_v,
                         (int64_t)align_up(f->sizes.n_params, 4), f->desc.lr, f->desc.beta1, f->desc.beta2,
                         f->desc.adam_eps, f->desc.growth_interval, st), "train_step adam");
     return NH_OK;
+}
+
+extern "C" nh_status accumulate_step(nh_field* f, const nh_geometry* g, const nh_ray_batch* b, float* loss_dev,
+                                     void* ws, size_t ws_bytes, void* stream) {
+    nh_status s = check_batch(f, g, b, ws, ws_bytes, true, "accumulate_step");
+    if (s != NH_OK) return s;
+    if (b->n_rays == 0) {
+        if (loss_dev) NH_CUDA(cudaMemsetAsync(loss_dev, 0, sizeof(float), S(stream)), "accumulate_step");
+        return NH_OK;
+    }
+    const RayWs w = ray_ws(ws, b->n_rays, b->n_samples);
+    return run_accumulate(f, g, b->view, b->n_rays, b->pix, b->a_meas, b->n_samples, loss_dev, w, S(stream));
 }
 
 extern "C" nh_status train_step(nh_field* f, const nh_geometry* g, const nh_ray_batch* b, float* loss_dev,

@@ -88,6 +88,7 @@ _SIGS = {
     "step_workspace_bytes": (_I, [_P, _I, _I, C.POINTER(_SZ)]),
     "points_workspace_bytes": (_I, [_P, _I, C.POINTER(_SZ)]),
     "train_step": (_I, [_P, _P, C.POINTER(RayBatch), _P, _P, _SZ, _P]),
+    "accumulate_step": (_I, [_P, _P, C.POINTER(RayBatch), _P, _P, _SZ, _P]),
     "train_step_host": (_I, [_P, _P, _I, _I, _P, _P, _I, _P, _P, _SZ, _P]),
     "render_forward": (_I, [_P, _P, C.POINTER(RayBatch), _P, _P, _SZ, _P]),
     "render_backward": (_I, [_P, _P, C.POINTER(RayBatch), _P, _P, _SZ, _P]),
@@ -308,6 +309,13 @@ def train_step(field, geom, view, pix, a_meas, n_samples, loss_out, ws, stream=N
     b = _batch(view, pix, a_meas, n_samples)
     _check(load().train_step(field.handle, geom.handle, C.byref(b), _ptr(loss_out), _ptr(ws),
                              ws.numel() * 4, _stream(stream)), "train_step")
+
+
+def accumulate_step(field, geom, view, pix, a_meas, n_samples, loss_out, ws, stream=None):
+    """Forward + loss + backward into the field's gradients, no optimizer step."""
+    b = _batch(view, pix, a_meas, n_samples)
+    _check(load().accumulate_step(field.handle, geom.handle, C.byref(b), _ptr(loss_out), _ptr(ws),
+                                  ws.numel() * 4, _stream(stream)), "accumulate_step")
 
 
 def train_step_host(field, geom, view, pix_host, a_meas_host, n_samples, loss_host, ws, stream=None):
