@@ -59,22 +59,25 @@ __device__ __forceinline__ const void* table_base(const FieldArgs& fa) {
 }
 
 // Normalized Hash Encoder forward: hhat (or h when norm = none), per-group rstd, y.
-template <int D>
+// G = number of normalization groups held: 1 (one group or none) or D / 2 (per level);
+// kernels instantiated with G = 1 are only launched for the one-group modes.
+template <int D, int G = D / 2>
 __device__ __forceinline__ void nhe_forward(const FieldArgs& fa, const float* sp, const float* smask,
                                             const float (&h)[D], float (&hhat)[D],
-                                            float (&rstd)[D / 2], float (&y)[D]) {
+                                            float (&rstd)[G], float (&y)[D]) {
+    static_assert(G == 1 || G == D / 2, "normalization groups");
     if (fa.norm == NH_NORM_LN) {
         float r1[1];
         ln_stats<D, D>(h, fa.eps, hhat, r1);
 #pragma unroll
-        for (int g = 0; g < D / 2; g++) rstd[g] = r1[0];
-    } else if (fa.norm == NH_NORM_LN_PER_LEVEL) {
-        ln_stats<D, 2>(h, fa.eps, hhat, rstd);
+        for (int g = 0; g < G; g++) rstd[g] = r1[0];
+    } else if (G == D / 2 && fa.norm == NH_NORM_LN_PER_LEVEL) {
+        if constexpr (G == D / 2) ln_stats<D, 2>(h, fa.eps, hhat, rstd);
     } else {
 #pragma unroll
         for (int k = 0; k < D; k++) hhat[k] = h[k];
 #pragma unroll
-        for (int g = 0; g < D / 2; g++) rstd[g] = 1.f;
+        for (int g = 0; g < G; g++) rstd[g] = 1.f;
     }
     const bool affine = fa.norm != NH_NORM_NONE;
 #pragma unroll
@@ -306,10 +309,10 @@ __device__ __forceinline__ void warp_weight_grad(float* dzb, const float* stage,
 // dh enters as dL/dy and leaves as dL/dh; gamma / beta gradients are reduced across
 // the warp through `col` (32 x 32 floats of per-warp scratch): lane s stores element
 // k of its row at column k ^ s, conflict-free for both the writes and the column sums.
-template <int D>
+template <int D, int G>
 __device__ __forceinline__ void nhe_backward_scatter(const FieldArgs& fa, const float* sp, const float* smask,
                                                      float* sg, float* col, const float (&hhat)[D],
-                                                     const float (&rstd)[D / 2], float (&dh)[D], const float x[3],
+                                                     const float (&rstd)[G], float (&dh)[D], const float x[3],
                                                      bool active, int lane) {
 #pragma unroll
     for (int k = 0; k < D; k++) dh[k] *= smask[k];     // dL/d(gamma hhat + beta)
@@ -341,7 +344,7 @@ __device__ __forceinline__ void nhe_backward_scatter(const FieldArgs& fa, const 
             float r1[1] = {rstd[0]};
             ln_backward<D, D>(hhat, r1, dh);
         } else {
-            ln_backward<D, 2>(hhat, rstd, dh);
+            if constexpr (G == D / 2) ln_backward<D, 2>(hhat, rstd, dh);
         }
     }
     bool bad = false;
@@ -357,54 +360,59 @@ __device__ __forceinline__ void nhe_backward_scatter(const FieldArgs& fa, const 
     scatter_point<D / 2>(fa, x, row, lane);
 }
 
-// State of one training sample carried from the forward half to the backward half
-// (everything else is in tensor memory): FFMA path.
-template <int D>
+// State of one training sample carried from the forward half to the backward half:
+// FFMA path. Everything else waits in tensor memory (hhat, a_1 .. a_{H-1}) or, for
+// a_H, in the warp's stage tile of shared memory.
+template <int D, int G>
 struct FfmaCarry {
-    float rstd[D / 2];
-    float a[kW];   // a_H, input of the output layer
+    float rstd[G];     // normalization groups: 1 (one LayerNorm / none) or L (per level)
     float mu;
 };
 
 // Forward of one sample per lane with activations kept in TMEM (slot 0: hhat, slot
-// k: a_k); a_H stays in the carry.
-template <int D, typename TT>
+// k: a_k); a_H goes to row `lane` of the stage tile (wbuf), where the backward's
+// output layer reads it. All 32 lanes must call it together.
+template <int D, int G, typename TT>
 __device__ __forceinline__ void ffma_forward(const FieldArgs& fa, const float* sp, const float* smask,
-                                             uint32_t tslot0, const float x[3], FfmaCarry<D>& s) {
+                                             float* wbuf, uint32_t tslot0, const float x[3], int lane,
+                                             FfmaCarry<D, G>& s) {
     constexpr int L = D / 2;
     const DenseLayout lay{D, fa.H};
     const int H = fa.H;
+    float a[kW];
     {
         float h[D], hhat[D], y[D];
         encode_point<L, TT>(fa, table_base<TT>(fa), x, h);
-        nhe_forward<D>(fa, sp, smask, h, hhat, s.rstd, y);
+        nhe_forward<D, G>(fa, sp, smask, h, hhat, s.rstd, y);
         tmem_st(tslot0, hhat);
         float z[kW];
         linear_fwd<D, kW>(sp + lay.W(0), sp + lay.b(0), y, z);
 #pragma unroll
-        for (int j = 0; j < kW; j++) s.a[j] = fmaxf(z[j], 0.f);
+        for (int j = 0; j < kW; j++) a[j] = fmaxf(z[j], 0.f);
     }
 #pragma unroll 1
     for (int k = 1; k < H; k++) {
-        tmem_st(tslot0 + 32 * k, s.a);
+        tmem_st(tslot0 + 32 * k, a);
         float z[kW];
-        linear_fwd<kW, kW>(sp + lay.W(k), sp + lay.b(k), s.a, z);
+        linear_fwd<kW, kW>(sp + lay.W(k), sp + lay.b(k), a, z);
 #pragma unroll
-        for (int j = 0; j < kW; j++) s.a[j] = fmaxf(z[j], 0.f);
+        for (int j = 0; j < kW; j++) a[j] = fmaxf(z[j], 0.f);
     }
     const float* wo = sp + lay.W(H);
     float zo = sp[lay.b(H)];
 #pragma unroll
-    for (int j = 0; j < kW; j++) zo = fmaf(wo[j], s.a[j], zo);
+    for (int j = 0; j < kW; j++) zo = fmaf(wo[j], a[j], zo);
     s.mu = 1.f / (1.f + expf(-zo));
+    __syncwarp();   // the previous sample's readers of the stage tile are done
+    stage_row<kW>(wbuf, lane, a);
 }
 
 // Backward of one sample per lane given dL/dmu (already multiplied by the loss
 // scale; 0 for lanes without a sample). All 32 lanes must call it together.
-template <int D, typename TT>
+template <int D, int G, typename TT>
 __device__ __forceinline__ void ffma_backward(const FieldArgs& fa, const float* sp, const float* smask, float* sg,
                                               float* wbuf, uint32_t tslot0, const float x[3], bool active, int lane,
-                                              const FfmaCarry<D>& s, float dmu) {
+                                              const FfmaCarry<D, G>& s, float dmu) {
     const DenseLayout lay{D, fa.H};
     const int H = fa.H;
     float* stage = wbuf;
@@ -413,9 +421,12 @@ __device__ __forceinline__ void ffma_backward(const FieldArgs& fa, const float* 
     const float dzo = dmu * mu * (1.f - mu);
     const float* wo = sp + lay.W(H);
 
-    // output layer: dW_H[0][i] = sum_s dzo[s] a_H[s][i], db_H = sum_s dzo[s]
-    stage_row<kW>(stage, lane, s.a);
+    // output layer: dW_H[0][i] = sum_s dzo[s] a_H[s][i], db_H = sum_s dzo[s]; the
+    // stage tile holds a_H from the forward
     dzb[lane] = dzo;
+    float dz[kW];
+#pragma unroll
+    for (int j = 0; j < kW; j++) dz[j] = (stage[lane * (kW + 1) + j] > 0.f) ? wo[j] * dzo : 0.f;
     __syncwarp();
     {
         float acc = 0.f;
@@ -426,9 +437,6 @@ __device__ __forceinline__ void ffma_backward(const FieldArgs& fa, const float* 
         if (lane == 0) atomicAdd(sg + lay.b(H), bs);
     }
     __syncwarp();
-    float dz[kW];
-#pragma unroll
-    for (int j = 0; j < kW; j++) dz[j] = (s.a[j] > 0.f) ? wo[j] * dzo : 0.f;
 
     // hidden layers k = H-1 .. 1: input a_k from TMEM
 #pragma unroll 1
@@ -461,49 +469,66 @@ __device__ __forceinline__ void ffma_backward(const FieldArgs& fa, const float* 
     }
     float dh[D];
     linear_bwd_data<D, kW>(sp + lay.W(0), dz, dh);   // dh <- dL/dy
-    nhe_backward_scatter<D>(fa, sp, smask, sg, dzb, hhat, s.rstd, dh, x, active, lane);
+    nhe_backward_scatter<D, G>(fa, sp, smask, sg, dzb, hhat, s.rstd, dh, x, active, lane);
 }
 
 // Forward then backward of one sample per lane; dmu_of(mu) gives dL/dmu.
-template <int D, typename TT, class DmuFn>
+template <int D, int G, typename TT, class DmuFn>
 __device__ __forceinline__ float sample_fwd_bwd(const FieldArgs& fa, const float* sp, const float* smask,
                                                 float* sg, float* wbuf, uint32_t tslot0, const float x[3],
                                                 bool active, int lane, DmuFn dmu_of) {
-    FfmaCarry<D> s;
-    ffma_forward<D, TT>(fa, sp, smask, tslot0, x, s);
-    ffma_backward<D, TT>(fa, sp, smask, sg, wbuf, tslot0, x, active, lane, s, active ? dmu_of(s.mu) : 0.f);
+    FfmaCarry<D, G> s;
+    ffma_forward<D, G, TT>(fa, sp, smask, wbuf, tslot0, x, lane, s);
+    ffma_backward<D, G, TT>(fa, sp, smask, sg, wbuf, tslot0, x, active, lane, s, active ? dmu_of(s.mu) : 0.f);
     return s.mu;
 }
 
 // Tensor-core path: the MLP of the warp's 32 samples runs on tensor cores
 // (nh_field_mma.cuh); encoding, normalization, LN backward and the scatter are the
-// per-sample float32 code. All 32 lanes must call these together.
-template <int D>
+// per-sample float32 code. All 32 lanes must call these together. The last hidden
+// layer's pre-activation fragments are parked in tensor memory after the layer
+// inputs (column 32 + 16 H), so that only mu and the normalization statistics stay
+// in registers between the forward and the backward.
+template <int D, int G>
 struct MmaCarry {
-    float rstd[D / 2];
-    float C[2][4][4];   // last hidden layer pre-activations (fragments)
+    float rstd[G];
     float mu;
 };
 
-template <int D, typename TT>
+__device__ __forceinline__ void frag_st(uint32_t taddr, const float (&C)[2][4][4]) {
+    float v[32];
+#pragma unroll
+    for (int i = 0; i < 32; i++) v[i] = C[i >> 4][(i >> 2) & 3][i & 3];
+    tmem_st(taddr, v);
+}
+__device__ __forceinline__ void frag_ld(uint32_t taddr, float (&C)[2][4][4]) {
+    float v[32];
+    tmem_ld(taddr, v);
+#pragma unroll
+    for (int i = 0; i < 32; i++) C[i >> 4][(i >> 2) & 3][i & 3] = v[i];
+}
+
+template <int D, int G, typename TT>
 __device__ __forceinline__ void mma_forward(const FieldArgs& fa, const float* sp, const uint16_t* sw,
                                             const float* smask, float* wbuf, uint32_t tslot0, const float x[3],
-                                            int lane, MmaCarry<D>& s) {
+                                            int lane, MmaCarry<D, G>& s) {
     constexpr int L = D / 2;
     const DenseLayout lay{D, fa.H};
     uint16_t* tile = reinterpret_cast<uint16_t*>(wbuf);
     float* rowbuf = reinterpret_cast<float*>(tile + 2 * kTile16);
     float h[D], hhat[D], y[D];
     encode_point<L, TT>(fa, table_base<TT>(fa), x, h);
-    nhe_forward<D>(fa, sp, smask, h, hhat, s.rstd, y);
+    nhe_forward<D, G>(fa, sp, smask, h, hhat, s.rstd, y);
     tmem_st(tslot0, hhat);
-    s.mu = mlp_mu_mma<TT, D, true>(lay, sp, sw, y, tile, rowbuf, lane, tslot0 + 32, s.C);
+    float C[2][4][4];
+    s.mu = mlp_mu_mma<TT, D, true>(lay, sp, sw, y, tile, rowbuf, lane, tslot0 + 32, C);
+    frag_st(tslot0 + 32 + 16 * fa.H, C);
 }
 
-template <int D, typename TT>
+template <int D, int G, typename TT>
 __device__ __forceinline__ void mma_backward(const FieldArgs& fa, const float* sp, const uint16_t* sw,
                                              const float* smask, float* sg, float* wbuf, uint32_t tslot0,
-                                             const float x[3], bool active, int lane, const MmaCarry<D>& s,
+                                             const float x[3], bool active, int lane, const MmaCarry<D, G>& s,
                                              float dmu) {
     const DenseLayout lay{D, fa.H};
     uint16_t* tile = reinterpret_cast<uint16_t*>(wbuf);
@@ -511,28 +536,33 @@ __device__ __forceinline__ void mma_backward(const FieldArgs& fa, const float* s
     float* rowbuf = reinterpret_cast<float*>(dztile + kTile16);
     const float dzo = dmu * s.mu * (1.f - s.mu);
     float dz[2][4][4];
-    out_layer_backward_mma<4>(lay, sp, sg, rowbuf, lane, dzo, s.C, dz);
+    {
+        float C[2][4][4];
+        frag_ld(tslot0 + 32 + 16 * fa.H, C);
+        out_layer_backward_mma<4>(lay, sp, sg, rowbuf, lane, dzo, C, dz);
+    }
     float dh[D];
     mlp_backward_mma<TT, D>(lay, sw, sg, tile, dztile, lane, tslot0 + 32, dz, dh);
     float hhat[D];
     tmem_ld(tslot0, hhat);
-    nhe_backward_scatter<D>(fa, sp, smask, sg, wbuf, hhat, s.rstd, dh, x, active, lane);
+    nhe_backward_scatter<D, G>(fa, sp, smask, sg, wbuf, hhat, s.rstd, dh, x, active, lane);
 }
 
-template <int D, typename TT, class DmuFn>
+template <int D, int G, typename TT, class DmuFn>
 __device__ __forceinline__ float sample_fwd_bwd_mma(const FieldArgs& fa, const float* sp, const uint16_t* sw,
                                                     const float* smask, float* sg, float* wbuf, uint32_t tslot0,
                                                     const float x[3], bool active, int lane, DmuFn dmu_of) {
-    MmaCarry<D> s;
-    mma_forward<D, TT>(fa, sp, sw, smask, wbuf, tslot0, x, lane, s);
-    mma_backward<D, TT>(fa, sp, sw, smask, sg, wbuf, tslot0, x, active, lane, s, active ? dmu_of(s.mu) : 0.f);
+    MmaCarry<D, G> s;
+    mma_forward<D, G, TT>(fa, sp, sw, smask, wbuf, tslot0, x, lane, s);
+    mma_backward<D, G, TT>(fa, sp, sw, smask, sg, wbuf, tslot0, x, active, lane, s, active ? dmu_of(s.mu) : 0.f);
     return s.mu;
 }
 
 // TMEM columns of one thread: FFMA path 32 H (hhat, a_1 .. a_{H-1}); tensor-core
-// path 32 + 16 H (hhat, then A fragments of every layer input).
+// path 64 + 16 H (hhat, the A fragments of every layer input, the last hidden
+// layer's pre-activations).
 __host__ __device__ inline int bwd_cols_per_thread(int precision, int H) {
-    return precision == NH_PREC_F32 ? 32 * H : mma_tmem_cols_per_thread(H);
+    return precision == NH_PREC_F32 ? 32 * H : mma_tmem_cols_per_thread(H) + 32;
 }
 // TMEM columns per CTA: two lane-quarter groups of warps, rounded to a power of two.
 static uint32_t bwd_tmem_cols(const FieldArgs& fa) {
@@ -594,13 +624,13 @@ __device__ __forceinline__ BwdCta bwd_begin(const FieldArgs& fa, float* smem, ui
 }
 
 // One training sample per lane through the FFMA or the tensor-core MLP.
-template <int D, typename TT, class DmuFn>
+template <int D, int G, typename TT, class DmuFn>
 __device__ __forceinline__ float train_sample(const FieldArgs& fa, const BwdCta& c, const float x[3], bool active,
                                               int lane, DmuFn dmu_of) {
     if constexpr (kMmaPath<TT>)
-        return sample_fwd_bwd_mma<D, TT>(fa, c.sp, c.sw, c.smask, c.sg, c.wbuf, c.tslot0, x, active, lane, dmu_of);
+        return sample_fwd_bwd_mma<D, G, TT>(fa, c.sp, c.sw, c.smask, c.sg, c.wbuf, c.tslot0, x, active, lane, dmu_of);
     else
-        return sample_fwd_bwd<D, TT>(fa, c.sp, c.smask, c.sg, c.wbuf, c.tslot0, x, active, lane, dmu_of);
+        return sample_fwd_bwd<D, G, TT>(fa, c.sp, c.smask, c.sg, c.wbuf, c.tslot0, x, active, lane, dmu_of);
 }
 
 __device__ __forceinline__ void bwd_end(const FieldArgs& fa, const BwdCta& c, uint32_t tcols) {
@@ -627,7 +657,7 @@ __device__ __forceinline__ void bwd_end(const FieldArgs& fa, const BwdCta& c, ui
     }
 }
 
-template <int D, typename TT>
+template <int D, int G, typename TT>
 __global__ void __launch_bounds__(kBwdWarps * 32, 2)
 k_ray_backward(FieldArgs fa, ViewArgs va, const int32_t* __restrict__ pix, int R, int N, int C,
                const float* __restrict__ dLdA, uint32_t tcols) {
@@ -647,7 +677,7 @@ k_ray_backward(FieldArgs fa, ViewArgs va, const int32_t* __restrict__ pix, int R
         float x[3];
         sample_position(g, active ? i : N - 1, x);
         const float gr = dLdA[r] * g.delta * scale;
-        train_sample<D, TT>(fa, cta, x, active, lane, [gr](float) { return gr; });
+        train_sample<D, G, TT>(fa, cta, x, active, lane, [gr](float) { return gr; });
     }
     bwd_end(fa, cta, tcols);
 }
@@ -660,22 +690,22 @@ k_ray_backward(FieldArgs fa, ViewArgs va, const int32_t* __restrict__ pix, int R
 // loss term and dL/dA_r (MSE or L1, Eq. 3) in shared memory, and every warp carries
 // on with the backward of the same samples. Ray-tile losses are accumulated in ray
 // order per CTA; k_train_loss adds the CTA partials in order.
-template <int D, typename TT>
+template <int D, int G, typename TT>
 struct TrainCarry {
-    using type = FfmaCarry<D>;
+    using type = FfmaCarry<D, G>;
 };
 
-template <int D>
-struct TrainCarry<D, __nv_bfloat16> {
-    using type = MmaCarry<D>;
+template <int D, int G>
+struct TrainCarry<D, G, __nv_bfloat16> {
+    using type = MmaCarry<D, G>;
 };
 
-template <int D>
-struct TrainCarry<D, __half> {
-    using type = MmaCarry<D>;
+template <int D, int G>
+struct TrainCarry<D, G, __half> {
+    using type = MmaCarry<D, G>;
 };
 
-template <int D, typename TT>
+template <int D, int G, typename TT>
 __global__ void __launch_bounds__(kBwdWarps * 32, 2)
 k_ray_train(FieldArgs fa, ViewArgs va, const int32_t* __restrict__ pix, const float* __restrict__ a_meas, int R,
             int N, int C, int rpr, int loss_kind, float* __restrict__ loss_part, uint32_t tcols) {
@@ -701,14 +731,14 @@ k_ray_train(FieldArgs fa, ViewArgs va, const int32_t* __restrict__ pix, const fl
         const int i = c * 32 + lane;
         const bool active = work && i < N;
         float x[3] = {0.f, 0.f, 0.f};
-        typename TrainCarry<D, TT>::type st;
+        typename TrainCarry<D, G, TT>::type st;
         st.mu = 0.f;
         if (work) {
             sample_position(g, i < N ? i : N - 1, x);
             if constexpr (kMmaPath<TT>)
-                mma_forward<D, TT>(fa, cta.sp, cta.sw, cta.smask, cta.wbuf, cta.tslot0, x, lane, st);
+                mma_forward<D, G, TT>(fa, cta.sp, cta.sw, cta.smask, cta.wbuf, cta.tslot0, x, lane, st);
             else
-                ffma_forward<D, TT>(fa, cta.sp, cta.smask, cta.tslot0, x, st);
+                ffma_forward<D, G, TT>(fa, cta.sp, cta.smask, cta.wbuf, cta.tslot0, x, lane, st);
         }
         const float part = warp_sum(active ? st.mu : 0.f) * (work ? g.delta : 0.f);
         if (lane == 0) s_part[warp] = part;
@@ -737,10 +767,10 @@ k_ray_train(FieldArgs fa, ViewArgs va, const int32_t* __restrict__ pix, const fl
         if (work) {
             const float dmu = active ? s_g[rl] * g.delta : 0.f;
             if constexpr (kMmaPath<TT>)
-                mma_backward<D, TT>(fa, cta.sp, cta.sw, cta.smask, cta.sg, cta.wbuf, cta.tslot0, x, active, lane, st,
+                mma_backward<D, G, TT>(fa, cta.sp, cta.sw, cta.smask, cta.sg, cta.wbuf, cta.tslot0, x, active, lane, st,
                                     dmu);
             else
-                ffma_backward<D, TT>(fa, cta.sp, cta.smask, cta.sg, cta.wbuf, cta.tslot0, x, active, lane, st, dmu);
+                ffma_backward<D, G, TT>(fa, cta.sp, cta.smask, cta.sg, cta.wbuf, cta.tslot0, x, active, lane, st, dmu);
         }
     }
     bwd_end(fa, cta, tcols);
@@ -781,7 +811,7 @@ __global__ void __launch_bounds__(128) k_points(FieldArgs fa, int n, const float
 
 // MCI fit: forward + backward of the voxel L1 loss (Eq. 2) in one pass, one CTA
 // partial of sum |mu - mu_gt| per block.
-template <int D, typename TT>
+template <int D, int G, typename TT>
 __global__ void __launch_bounds__(kBwdWarps * 32, 2)
 k_points_fit(FieldArgs fa, int n, const float* __restrict__ xyz, const float* __restrict__ mu_gt,
              float* __restrict__ loss_part, uint32_t tcols) {
@@ -800,7 +830,7 @@ k_points_fit(FieldArgs fa, int n, const float* __restrict__ xyz, const float* __
         const long long pc = active ? p : (long long)n - 1;
         const float x[3] = {xyz[3 * pc], xyz[3 * pc + 1], xyz[3 * pc + 2]};
         const float gt = mu_gt[pc];
-        const float mu = train_sample<D, TT>(fa, cta, x, active, lane, [gt, scale](float m) {
+        const float mu = train_sample<D, G, TT>(fa, cta, x, active, lane, [gt, scale](float m) {
             const float r = m - gt;
             return (r > 0.f ? scale : (r < 0.f ? -scale : 0.f));
         });
@@ -989,6 +1019,19 @@ static long long train_grid(K kernel, size_t smem, uint32_t tcols, long long nee
         else return cudaErrorInvalidValue;                          \
     } while (0)
 
+// Training kernels are also specialised on the number of normalization groups G
+// (one statistic per level for the per-level LayerNorm, else one), which sets how
+// many registers carry the statistics from the forward to the backward.
+#define NH_DISPATCH_DG(fa, ...)                                                          \
+    do {                                                                                 \
+        const bool per_level_ = (fa).norm == NH_NORM_LN_PER_LEVEL;                       \
+        if ((fa).D == 16 && per_level_) { constexpr int D_ = 16, G_ = 8; __VA_ARGS__; }  \
+        else if ((fa).D == 16) { constexpr int D_ = 16, G_ = 1; __VA_ARGS__; }           \
+        else if ((fa).D == 32 && per_level_) { constexpr int D_ = 32, G_ = 16; __VA_ARGS__; } \
+        else if ((fa).D == 32) { constexpr int D_ = 32, G_ = 1; __VA_ARGS__; }           \
+        else return cudaErrorInvalidValue;                                               \
+    } while (0)
+
 template <typename TT>
 cudaError_t launch_ray_forward_tt(const FieldArgs& fa, const ViewArgs& va, const int32_t* pix, int R, int N,
                                   float* ray_part, cudaStream_t st) {
@@ -1014,8 +1057,8 @@ cudaError_t launch_ray_backward_tt(const FieldArgs& fa, const ViewArgs& va, cons
     if (tasks == 0) return cudaSuccess;
     const size_t sm = bwd_smem_bytes(fa);
     const uint32_t tcols = bwd_tmem_cols(fa);
-    NH_DISPATCH_D(fa, {
-        auto k = k_ray_backward<D_, TT>;
+    NH_DISPATCH_DG(fa, {
+        auto k = k_ray_backward<D_, G_, TT>;
         cudaError_t e = set_smem(k, sm);
         if (e != cudaSuccess) return e;
         const long long blocks = train_grid(k, sm, tcols, (tasks + kBwdWarps - 1) / kBwdWarps);
@@ -1042,8 +1085,8 @@ cudaError_t launch_points_tt(const FieldArgs& fa, int n, const float* xyz, const
     }
     const size_t sm = bwd_smem_bytes(fa);
     const uint32_t tcols = bwd_tmem_cols(fa);
-    NH_DISPATCH_D(fa, {
-        auto k = k_points_fit<D_, TT>;
+    NH_DISPATCH_DG(fa, {
+        auto k = k_points_fit<D_, G_, TT>;
         cudaError_t e = set_smem(k, sm);
         if (e != cudaSuccess) return e;
         long long blocks = train_grid(k, sm, tcols, ((long long)n + 32 * kBwdWarps - 1) / (32 * kBwdWarps));
@@ -1092,8 +1135,8 @@ cudaError_t launch_ray_train_tt(const FieldArgs& fa, const ViewArgs& va, const i
     const long long ngroups = ((long long)R + rpr - 1) / rpr;
     const size_t sm = bwd_smem_bytes(fa);
     const uint32_t tcols = bwd_tmem_cols(fa);
-    NH_DISPATCH_D(fa, {
-        auto k = k_ray_train<D_, TT>;
+    NH_DISPATCH_DG(fa, {
+        auto k = k_ray_train<D_, G_, TT>;
         cudaError_t e = set_smem(k, sm);
         if (e != cudaSuccess) return e;
         long long blocks = train_grid(k, sm, tcols, ngroups, threads);

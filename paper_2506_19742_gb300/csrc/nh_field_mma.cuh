@@ -6,6 +6,7 @@
 // Tensor-memory layout of one thread (row = sample) in the training kernels:
 //   columns [0, 32)        hhat (float, D values)
 //   columns 32 + 16 l ...  A fragments (16 x 32-bit) of layer l's input, l < H
+//   columns 32 + 16 H ...  the last hidden layer's pre-activations (32 floats)
 // Per-warp shared scratch: a 16-bit [32][kWS] activation tile, a 16-bit [32][kWS]
 // dz tile (aliased by a float [32][D+2] dy tile and the LN-gradient transpose),
 // and a 32-float row buffer.
@@ -170,43 +171,26 @@ __device__ __forceinline__ void mlp_backward_mma(const DenseLayout& lay, const u
         // db_l; dz as hi + lo 16-bit fragments: the data gradient uses both (so the
         // rounding does not compound along the chain), the dz tile holds hi
         add_colsum<4>(dz, sg + lay.b(l), lane);
-        uint32_t Adz[2][2][4];
-        float din[2][4][4];
+        uint32_t Adz[2][2][4], Adl[2][2][4];
+        pack_afrag_split<T>(dz, Adz, Adl);
         {
-            uint32_t Adl[2][2][4];
-            pack_afrag_split<T>(dz, Adz, Adl);
-            // data gradient din[s][i] = sum_j dz[s][j] W[j][i]  (B = W^T rows)
+            // layer input fragments from tensor memory into the activation tile
+            uint32_t Aact[2][2][4];
+            tm_ld_u32<16>(tcol0 + 16 * l, &Aact[0][0][0]);
+            __syncwarp();
+            store_afrag<2>(dztile, lane, Adz);
             if (first && D == 16) {
-                float d2[2][2][4];
-                mma_layer<T, 2, 2>(Wt, nullptr, Adz, lane, d2);
-                mma_accumulate<T, 2, 2>(Wt, Adl, lane, d2);
+                uint32_t A1[2][1][4];
 #pragma unroll
                 for (int mt = 0; mt < 2; mt++)
 #pragma unroll
-                    for (int nt = 0; nt < 4; nt++)
-#pragma unroll
-                        for (int c = 0; c < 4; c++) din[mt][nt][c] = nt < 2 ? d2[mt][nt][c] : 0.f;
+                    for (int rr = 0; rr < 4; rr++) A1[mt][0][rr] = Aact[mt][0][rr];
+                store_afrag<1>(tile, lane, A1);
             } else {
-                mma_layer<T, 2, 4>(Wt, nullptr, Adz, lane, din);
-                mma_accumulate<T, 2, 4>(Wt, Adl, lane, din);
+                store_afrag<2>(tile, lane, Aact);
             }
+            __syncwarp();
         }
-        // layer input fragments from tensor memory
-        uint32_t Aact[2][2][4];
-        tm_ld_u32<16>(tcol0 + 16 * l, &Aact[0][0][0]);
-        __syncwarp();
-        store_afrag<2>(dztile, lane, Adz);
-        if (first && D == 16) {
-            uint32_t A1[2][1][4];
-#pragma unroll
-            for (int mt = 0; mt < 2; mt++)
-#pragma unroll
-                for (int rr = 0; rr < 4; rr++) A1[mt][0][rr] = Aact[mt][0][rr];
-            store_afrag<1>(tile, lane, A1);
-        } else {
-            store_afrag<2>(tile, lane, Aact);
-        }
-        __syncwarp();
         // dW_l[j][i] = sum_s dz[s][j] act[s][i]: A = dz^T (m = j, k = s), B = act (k = s, n = i),
         // one 16-row half of j at a time
         {
@@ -249,8 +233,27 @@ __device__ __forceinline__ void mlp_backward_mma(const DenseLayout& lay, const u
                 }
             }
         }
+        // data gradient din[s][i] = sum_j dz[s][j] W[j][i] (B = W^T rows), from the
+        // hi and lo parts of dz so that the rounding does not compound along the chain
+        float din[2][4][4];
+        if (first && D == 16) {
+            float d2[2][2][4];
+            mma_layer<T, 2, 2>(Wt, nullptr, Adz, lane, d2);
+            mma_accumulate<T, 2, 2>(Wt, Adl, lane, d2);
+#pragma unroll
+            for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+                for (int nt = 0; nt < 4; nt++)
+#pragma unroll
+                    for (int c = 0; c < 4; c++) din[mt][nt][c] = nt < 2 ? d2[mt][nt][c] : 0.f;
+        } else {
+            mma_layer<T, 2, 4>(Wt, nullptr, Adz, lane, din);
+            mma_accumulate<T, 2, 4>(Wt, Adl, lane, din);
+        }
         if (!first) {
-            // ReLU mask of layer l's input, read from its A fragments
+            // ReLU mask of layer l's input, read again from its A fragments
+            uint32_t Aact[2][2][4];
+            tm_ld_u32<16>(tcol0 + 16 * l, &Aact[0][0][0]);
 #pragma unroll
             for (int mt = 0; mt < 2; mt++)
 #pragma unroll
