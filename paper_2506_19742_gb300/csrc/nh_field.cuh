@@ -705,8 +705,11 @@ struct TrainCarry<D, G, __half> {
     using type = MmaCarry<D, G>;
 };
 
-template <int D, int G, typename TT>
-__global__ void __launch_bounds__(kBwdWarps * 32, 2)
+// NW: most warps a CTA launches with; CTAs of at most six warps (rays of three,
+// five or six chunks) are compiled with the register budget of two six-warp CTAs
+// per SM instead of two eight-warp ones.
+template <int D, int G, typename TT, int NW>
+__global__ void __launch_bounds__(NW * 32, 2)
 k_ray_train(FieldArgs fa, ViewArgs va, const int32_t* __restrict__ pix, const float* __restrict__ a_meas, int R,
             int N, int C, int rpr, int loss_kind, float* __restrict__ loss_part, uint32_t tcols) {
     extern __shared__ __align__(16) float smem[];
@@ -1136,7 +1139,7 @@ cudaError_t launch_ray_train_tt(const FieldArgs& fa, const ViewArgs& va, const i
     const size_t sm = bwd_smem_bytes(fa);
     const uint32_t tcols = bwd_tmem_cols(fa);
     NH_DISPATCH_DG(fa, {
-        auto k = k_ray_train<D_, G_, TT>;
+        auto k = threads <= 6 * 32 ? k_ray_train<D_, G_, TT, 6> : k_ray_train<D_, G_, TT, kBwdWarps>;
         cudaError_t e = set_smem(k, sm);
         if (e != cudaSuccess) return e;
         long long blocks = train_grid(k, sm, tcols, ngroups, threads);
