@@ -311,6 +311,31 @@ def run_mci(args):
     print(json.dumps(line))
 
 
+class Ranks:
+    """Barrier and max over the job's ranks (one process per GPU); with no process
+    group both are no-ops."""
+
+    def __init__(self, dist, device):
+        self.dist, self.device = dist, device
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def allmax(self, x: float) -> float:
+        if self.dist is None:
+            return x
+        import torch
+        t = torch.tensor([x], device=self.device, dtype=torch.float64)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+
+def job_value(samples_per_rank: int, world: int, ms_max: float) -> float:
+    """Whole-job throughput: every rank's samples over the slowest rank's time."""
+    return float(samples_per_rank) * world / (ms_max / 1e3)
+
+
 def run_ours(args, rank: int, world: int, local_rank: int):
     import torch
     from paper_2506_19742_gb300 import build as nhbuild
@@ -324,16 +349,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def allmax(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    ranks = Ranks(dist, dev)
+    barrier, allmax = ranks.barrier, ranks.allmax
 
     w = S.WORKLOADS[args.workload]
     seed = args.seed + 1000 * rank
@@ -377,7 +394,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     clocks = clk.summary()
     ms = allmax(ms)
     samples_all = float(R * N * K * world)
-    value = samples_all / (ms / 1e3)
+    value = job_value(R * N * K, world, ms)
 
     # per-kernel durations (CUDA events on the launching stream) for the roofline
     stream = torch.cuda.current_stream()

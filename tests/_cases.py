@@ -51,5 +51,27 @@ def rounded_tables(flat, cfg, precision):
     return out
 
 
+# Seeded 16^3 sub-instance of the large configuration: the L16 F2 16..2048 field with
+# T = 2^8 (level 0 dense, every other level hashed with forced collisions), one
+# LayerNorm and the 4x32 MLP, on 4 views of an 8x8 detector.
+C4_SUB = S.FieldConfig(n_levels=16, n_feat=2, log2_T=8, base_res=16, max_res=2048, norm=S.NORM_LN,
+                       hidden_layers=4, width=32)
+C4_SUB_GEOM = S.GeometryConfig(n_views=4, det_nu=8, det_nv=8)
+C4_SUB_N = 16
+
+
+def c4_subinstance(seed=11):
+    """(oracle geometry, float64 params, pix, A_meas): measurements are the oracle
+    projections (view 1) of a 16^3 shell phantom of the large workload's family, 6
+    rays that meet the volume and one that misses."""
+    geom = oracle_geom(C4_SUB_GEOM)
+    vol, _ = S.phantom(S.WORKLOADS["large_bf16"], seed, D=16)
+    proj = oracle.project(geom, vol, oversample=2)
+    pix = batch(C4_SUB_GEOM, 1, 6, seed, n_miss=1)
+    A_meas = proj[1].reshape(-1)[pix]
+    flat = S.init_params(C4_SUB, seed, table_scale=0.5).astype(np.float64)
+    return geom, flat, pix, A_meas
+
+
 def replace(cfg, **kw):
     return dataclasses.replace(cfg, **kw)

@@ -13,7 +13,8 @@ import pytest
 
 import oracle
 import synthetic as S
-from _cases import batch, field_cfg, hit_pixels, oracle_geom, replace, rounded_tables
+from _cases import (C4_SUB, C4_SUB_GEOM, C4_SUB_N, batch, c4_subinstance, field_cfg, hit_pixels, oracle_geom,
+                    replace, rounded_tables)
 
 pytestmark = pytest.mark.gpu
 
@@ -258,6 +259,36 @@ def test_mixed_precision_forward_and_gradients_track_oracle(lib, precision, case
     _grad_close(g, oracle.render_backward(cache, dLdA, cfg), cfg, what=f"mixed {precision}", norm_rtol=tol_g)
 
 
+@pytest.mark.parametrize("precision", [S.PREC_F32, S.PREC_BF16])
+def test_c4_subinstance_gradients_match_oracle(lib, precision):
+    """The large configuration's field shape (L16, 16..2048, T = 2^8 with forced
+    collisions, 4x32 MLP) on the seeded 16^3 sub-instance whose oracle gradient is
+    pinned by central differences: the library's backward gives the oracle gradient
+    (FP32 within 1e-3 of each group's largest entry; BF16 within the mixed-precision
+    norm bound) and the oracle loss."""
+    cfg = replace(C4_SUB, precision=precision)
+    og, flat64, pix, A_meas = c4_subinstance()
+    flat = flat64.astype(np.float32)
+    ref_flat = rounded_tables(flat, cfg, precision).astype(np.float64)
+    A, cache = oracle.render_forward(ref_flat, cfg, og, 1, pix, C4_SUB_N)
+    ref_loss, dLdA = oracle.loss_and_grad(A, A_meas, S.LOSS_MSE)
+    ref_grad = oracle.render_backward(cache, dLdA, cfg)
+    field = lib.Field(cfg, params=flat)
+    geom = lib.Geometry.from_config(C4_SUB_GEOM)
+    ws = lib.workspace(lib.step_workspace_bytes(field, len(pix), C4_SUB_N))
+    lib.render_backward(field, geom, 1, _t(pix), C4_SUB_N, _t(dLdA.astype(np.float32)), ws)
+    g = _np(field.flat_grads())
+    if precision == S.PREC_F32:
+        _grad_close(g, ref_grad, cfg, what="c4 sub f32")
+    else:
+        _grad_close(g, ref_grad, cfg, what="c4 sub bf16", norm_rtol=MIXED_TOL[precision][1])
+    field.grads.zero_()
+    loss_t = torch.zeros(1, device="cuda")
+    lib.accumulate_step(field, geom, 1, _t(pix), _t(A_meas.astype(np.float32)), C4_SUB_N, loss_t, ws)
+    tol = 1e-5 if precision == S.PREC_F32 else 2 * MIXED_TOL[precision][0]
+    assert abs(_np(loss_t)[0] - ref_loss) <= tol * ref_loss
+
+
 @pytest.mark.parametrize("precision", [S.PREC_BF16, S.PREC_F16])
 def test_mixed_precision_voxel_loss_and_query(lib, precision):
     cfg = field_cfg(n_levels=16, hidden_layers=4, log2_T=12, max_res=256, precision=precision,
@@ -408,6 +439,45 @@ def test_nonfinite_measurement_skips_the_step(lib):
     lib.train_step(field, geom, 0, _t(pix), _t(a_meas), 16, loss_t, ws)
     flags, _, step = field.poll_status()
     assert flags == 0 and step == 1
+
+
+def test_f16_dynamic_loss_scale_halves_on_overflow_and_grows_back(lib):
+    """Dynamic loss scaling of the FP16 path: a scale of 2^40 overflows the 16-bit
+    backward (non-finite dL/dh), so the step is skipped, the parameters stay as they
+    were and the scale halves, until a scale fits; a safe scale doubles after every
+    growth_interval applied steps."""
+    geom = lib.Geometry.from_config(GEOM)
+    pix = batch(GEOM, 0, 128, seed=2)
+    a_meas = np.random.default_rng(2).uniform(0, 0.8, size=len(pix)).astype(np.float32)
+    N = 48
+    cfg = field_cfg(precision=S.PREC_F16, loss_scale_init=2.0 ** 40, growth_interval=3)
+    flat = S.init_params(cfg, 12).astype(np.float32)
+    field = lib.Field(cfg, params=flat)
+    ws = lib.workspace(lib.step_workspace_bytes(field, len(pix), N))
+    loss_t = torch.zeros(1, device="cuda")
+    scale, skipped = 2.0 ** 40, 0
+    for _ in range(60):
+        lib.train_step(field, geom, 0, _t(pix), _t(a_meas), N, loss_t, ws)
+        flags, s, step = field.poll_status()
+        if not flags & lib.FLAG_SKIPPED:
+            assert flags == 0 and step == 1 and s == scale
+            break
+        assert flags & lib.FLAG_NONFINITE and step == 0 and s == scale / 2
+        assert np.array_equal(_np(field.flat_params()), flat)
+        assert float(field.grads.abs().max()) == 0.0
+        scale, skipped = s, skipped + 1
+    else:
+        raise AssertionError("the loss scale never came down to a finite step")
+    assert skipped >= 3 and scale == 2.0 ** (40 - skipped)
+    assert np.isfinite(_np(loss_t)[0])
+
+    cfg = replace(cfg, loss_scale_init=1024.0)
+    field = lib.Field(cfg, params=flat)
+    for k in range(1, 7):
+        lib.train_step(field, geom, 0, _t(pix), _t(a_meas), N, loss_t, ws)
+        flags, s, step = field.poll_status()
+        assert flags == 0 and step == k
+        assert s == 1024.0 * 2 ** (k // 3)
 
 
 def test_argument_errors_are_reported(lib):

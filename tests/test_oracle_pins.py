@@ -9,6 +9,7 @@ import pytest
 
 import oracle
 import synthetic as S
+from _cases import C4_SUB, C4_SUB_N, c4_subinstance
 
 TINY_F = S.FieldConfig(n_levels=2, n_feat=2, log2_T=8, base_res=2, max_res=8,
                        norm=S.NORM_LN, hidden_layers=2, width=8)
@@ -274,6 +275,24 @@ def test_render_gradient_finite_differences(norm):
     _, dLdA = oracle.loss_and_grad(A, A_meas, S.LOSS_MSE)
     grad = oracle.render_backward(cache, dLdA, cfg)
     _fd_check(loss, flat, grad, np.random.default_rng(1))
+
+
+def test_render_gradient_finite_differences_c4_subinstance():
+    """The backward (Sec. 2.5 training, Eq. 1 ray sum, LN, MLP, hash scatter with
+    collisions) agrees with central differences at the large configuration's field
+    shape."""
+    geom, flat, pix, A_meas = c4_subinstance()
+    N = C4_SUB_N
+    assert oracle.level_resolutions(16, 16, 2048)[-1] == 2048
+
+    def loss(fl):
+        return oracle.loss_and_grad(oracle.render(fl, C4_SUB, geom, 1, pix, N), A_meas, S.LOSS_MSE)[0]
+
+    A, cache = oracle.render_forward(flat, C4_SUB, geom, 1, pix, N)
+    assert A[-1] == 0.0 and np.all(A[:-1] != 0.0)
+    _, dLdA = oracle.loss_and_grad(A, A_meas, S.LOSS_MSE)
+    grad = oracle.render_backward(cache, dLdA, C4_SUB)
+    _fd_check(loss, flat, grad, np.random.default_rng(4), n_pick=200)
 
 
 def test_l1_pixel_loss_and_voxel_loss_gradients():
