@@ -56,6 +56,7 @@ def parse_args():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-psnr", action="store_true", help="skip the time-to-PSNR runs")
+    p.add_argument("--no-l2", action="store_true", help="skip the gather / scatter L2 roofline probes")
     p.add_argument("--psnr-steps", type=int, default=3000, help="step cap of the time-to-PSNR runs")
     p.add_argument("--experiment", default="", choices=["", "mci"])
     p.add_argument("--mci-cases", type=int, default=8)
@@ -336,6 +337,82 @@ def job_value(samples_per_rank: int, world: int, ms_max: float) -> float:
     return float(samples_per_rank) * world / (ms_max / 1e3)
 
 
+def event_ms(torch, fn, n=5, warm=1):
+    """Mean device time of fn() over n runs (CUDA events on the current stream)."""
+    stream = torch.cuda.current_stream()
+    for _ in range(warm):
+        fn()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    for a, b in evs:
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return float(np.mean([a.elapsed_time(b) for a, b in evs]))
+
+
+def l2_roofline(nh, torch, geom, fields, batch, N, dev):
+    """The gather and scatter stages alone (encode_points / scatter_points at one
+    batch's sample positions) against the chip's measured L2 capacity: streaming L2
+    read bandwidth, and the rates of uniformly random corner-sized loads and float2
+    atomics on tables of the stages' own sizes (the probe kernels). Fractions:
+    algorithmic bytes (L 8 F x element size per point) and 32-byte sectors per corner
+    over the L2 bandwidth, corner loads / atomics over the random-access probe rate."""
+    sink = torch.zeros(1, device=dev)
+    buf = torch.zeros(48 << 20 >> 2, device=dev)            # 48 MB: resident in the 126 MB L2
+    reps = 10
+    t = event_ms(torch, lambda: nh.probe_l2_read(buf, reps, sink))
+    l2_gbs = buf.numel() * 4 * reps / (t / 1e3) / 1e9
+    del buf
+    view, pix, _ = batch
+    R = pix.numel()
+    xyz = torch.empty(R * N * 3, device=dev)
+    delta = torch.empty(R, device=dev)
+    nh.sample_rays(geom, view, pix, N, xyz, delta)
+    n = R * N
+    out = {"l2_read_gbs": round(l2_gbs, 1), "points": n,
+           "method": "probe_l2_read of a 48 MB buffer x10 sweeps; probe_random_gather / probe_random_red "
+                     "on tables of the stage's size; encode_points / scatter_points at one batch's samples"}
+    for name, fld in fields.items():
+        cfg = fld.cfg
+        L, F = cfg.n_levels, cfg.n_feat
+        tb = 4 if cfg.precision == S.PREC_F32 else 2
+        corners = n * L * 8
+        h = torch.empty(n * L * F, device=dev)
+        t_g = event_ms(torch, lambda: nh.encode_points(fld, xyz, h))
+        table = fld.params if cfg.precision == S.PREC_F32 else fld.tables_lp
+        tbytes = L * cfg.T * F * tb
+        n_ent = 1 << ((L * cfg.T).bit_length() - 1)          # a power of two for the probe
+        tab = table.view(torch.uint8)[: n_ent * F * tb]
+        done = [0]
+
+        def gprobe():
+            done[0] = nh.probe_random_gather(tab, F * tb, corners, sink)
+        t_pg = event_ms(torch, gprobe)
+        gather = {"ms": round(t_g, 4), "corner_loads": corners,
+                  "algorithmic_gbs": round(corners * F * tb / (t_g / 1e3) / 1e9, 1),
+                  "sector_gbs": round(corners * 32 / (t_g / 1e3) / 1e9, 1),
+                  "probe_random_loads_per_s": done[0] / (t_pg / 1e3)}
+        gather["frac_l2_algorithmic"] = round(gather["algorithmic_gbs"] / l2_gbs, 4)
+        gather["frac_l2_sectors"] = round(gather["sector_gbs"] / l2_gbs, 4)
+        gather["frac_random_probe"] = round((corners / (t_g / 1e3)) / gather["probe_random_loads_per_s"], 4)
+        dh = torch.randn(n * L * F, device=dev) * 1e-3
+        t_s = event_ms(torch, lambda: nh.scatter_points(fld, xyz, dh))
+        gtab = fld.grads[: n_ent * F]
+
+        def rprobe():
+            done[0] = nh.probe_random_red(gtab, corners)
+        t_pr = event_ms(torch, rprobe)
+        fld.grads.zero_()
+        scatter = {"ms": round(t_s, 4), "corner_atomics": corners,
+                   "algorithmic_gbs": round(corners * F * 4 / (t_s / 1e3) / 1e9, 1),
+                   "probe_random_atomics_per_s": done[0] / (t_pr / 1e3)}
+        scatter["frac_l2_algorithmic"] = round(scatter["algorithmic_gbs"] / l2_gbs, 4)
+        scatter["frac_random_probe"] = round((corners / (t_s / 1e3)) / scatter["probe_random_atomics_per_s"], 4)
+        out[name] = {"table_mb": round(tbytes / 1e6, 1), "gather": gather, "scatter": scatter}
+    return out
+
+
 def run_ours(args, rank: int, world: int, local_rank: int):
     import torch
     from paper_2506_19742_gb300 import build as nhbuild
@@ -474,6 +551,13 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                      "ms_per_step": ms_m / K, "speedup_vs_fp32": (samples_all / (ms_m / 1e3)) / value,
                      "launch_ms": {"forward+loss+backward": round(tacc, 4), "adam": round(ta, 4)}}
 
+    l2 = None
+    if rank == 0 and not args.no_l2:
+        flds = {w.name: field}
+        if mixed is not None:
+            flds[mixed["workload"]] = field_m
+        l2 = l2_roofline(nh, torch, geom, flds, dev_batches[W], N, dev)
+
     # time to PSNR: FP32 and the mixed-precision workload on the same scan
     psnr = None
     if not args.no_psnr and rank == 0:
@@ -512,7 +596,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                          f"{4 * 4 * S.param_layout(f)['_total'][1] / 1e6:.0f} MB of parameter state",
                    "parallelism": f"replicas x{world}"},
         "clocks": clocks, "e2e": e2e, "gpu_launches": (4 if fused else 5) * K, "roofline": roofline, "cpu_baseline": cpu,
-        "mixed": mixed, "psnr": psnr, "final_loss": losses[-1] if losses else None,
+        "mixed": mixed, "l2_roofline": l2, "psnr": psnr, "final_loss": losses[-1] if losses else None,
     }
     print(json.dumps(line))
 

@@ -279,6 +279,33 @@ nh_status hash_corners(const nh_field* f, int32_t n, const float* xyz_dev, uint3
                        float* w_dev, void* stream);
 /* encode_points: trilinear hash features float[n][L * F] (the gather stage). */
 nh_status encode_points(const nh_field* f, int32_t n, const float* xyz_dev, float* h_dev, void* stream);
+/* scatter_points: the hash scatter stage (Sec. 2.5 backward into the tables of the
+ * hash encoding): for n points xyz_dev float[n][3] with upstream gradients dh_dev
+ * float[n][L * F] (16-byte aligned), adds w_k * dh[p][l F + f] into the field's
+ * float32 gradient table at every corner k of every level l. Accumulates; the
+ * caller zeroes the gradients when it wants a fresh sum. Addition order is not
+ * fixed (atomics). */
+nh_status scatter_points(nh_field* f, int32_t n, const float* xyz_dev, const float* dh_dev, void* stream);
+
+/* ------------------------------------------------------------------ roofline probes
+ * No counterpart in the paper: kernels that measure the chip's capacity for the
+ * access patterns of the gather and scatter stages, to be timed by the caller with
+ * CUDA events on `stream`. They compute nothing of the method.
+ * probe_l2_read: `reps` sweeps of 16-byte streaming reads over buf_dev (bytes a
+ *   non-zero multiple of 16, 16-byte aligned); the L2 bandwidth when the buffer
+ *   fits in L2 and the first sweep is not timed apart. sink_dev: one float that
+ *   is written only to keep the loads live.
+ * probe_random_gather: independent uniformly random loads of entry_bytes (4 or 8)
+ *   from table_dev of n_entries (a power of two <= 2^32), eight in flight per
+ *   thread; *n_done (host) receives the number issued (n_loads rounded up to the
+ *   launch's granularity).
+ * probe_random_red: uniformly random red.global.add.v2.f32 of 1e-30 into the
+ *   float2 entries of table_dev (n_entries a power of two, 8-byte aligned); the
+ *   table's values change. *n_done as above. */
+nh_status probe_l2_read(const void* buf_dev, uint64_t bytes, int32_t reps, float* sink_dev, void* stream);
+nh_status probe_random_gather(const void* table_dev, uint64_t n_entries, int32_t entry_bytes, int64_t n_loads,
+                              float* sink_dev, int64_t* n_done, void* stream);
+nh_status probe_random_red(float* table_dev, uint64_t n_entries, int64_t n_ops, int64_t* n_done, void* stream);
 
 #ifdef __cplusplus
 }

@@ -609,6 +609,45 @@ extern "C" nh_status encode_points(const nh_field* f, int32_t n, const float* xy
     return NH_OK;
 }
 
+extern "C" nh_status scatter_points(nh_field* f, int32_t n, const float* xyz, const float* dh, void* stream) {
+    if (!f || (n > 0 && (!xyz || !dh))) return fail(NH_ERR_INVALID_ARG, "scatter_points: null argument");
+    if (n < 0) return fail(NH_ERR_INVALID_ARG, "scatter_points: n < 0");
+    if (!aligned(dh, 16)) return fail(NH_ERR_ALIGNMENT, "scatter_points: dh must be 16-byte aligned");
+    NH_CUDA(launch_scatter_points(f->fa, n, xyz, dh, S(stream)), "scatter_points");
+    return NH_OK;
+}
+
+static bool pow2(uint64_t v) { return v != 0 && (v & (v - 1)) == 0; }
+
+extern "C" nh_status probe_l2_read(const void* buf, uint64_t bytes, int32_t reps, float* sink, void* stream) {
+    if (!buf || !sink) return fail(NH_ERR_INVALID_ARG, "probe_l2_read: null argument");
+    if (reps < 1 || bytes == 0 || bytes % 16 != 0)
+        return fail(NH_ERR_INVALID_ARG, "probe_l2_read: need reps >= 1 and a non-zero multiple of 16 bytes");
+    if (!aligned(buf, 16)) return fail(NH_ERR_ALIGNMENT, "probe_l2_read: buffer must be 16-byte aligned");
+    NH_CUDA(launch_probe_l2_read(buf, bytes, reps, sink, S(stream)), "probe_l2_read");
+    return NH_OK;
+}
+
+extern "C" nh_status probe_random_gather(const void* table, uint64_t n_entries, int32_t entry_bytes, int64_t n_loads,
+                                         float* sink, int64_t* n_done, void* stream) {
+    if (!table || !sink || !n_done) return fail(NH_ERR_INVALID_ARG, "probe_random_gather: null argument");
+    if (!pow2(n_entries) || n_entries > (uint64_t(1) << 32) || (entry_bytes != 4 && entry_bytes != 8) || n_loads < 0)
+        return fail(NH_ERR_INVALID_ARG, "probe_random_gather: n_entries a power of two <= 2^32, entry_bytes 4 or 8");
+    if (!aligned(table, (size_t)entry_bytes)) return fail(NH_ERR_ALIGNMENT, "probe_random_gather: misaligned table");
+    NH_CUDA(launch_probe_random_gather(table, n_entries, entry_bytes, n_loads, sink, n_done, S(stream)),
+            "probe_random_gather");
+    return NH_OK;
+}
+
+extern "C" nh_status probe_random_red(float* table, uint64_t n_entries, int64_t n_ops, int64_t* n_done, void* stream) {
+    if (!table || !n_done) return fail(NH_ERR_INVALID_ARG, "probe_random_red: null argument");
+    if (!pow2(n_entries) || n_entries > (uint64_t(1) << 32) || n_ops < 0)
+        return fail(NH_ERR_INVALID_ARG, "probe_random_red: n_entries a power of two <= 2^32");
+    if (!aligned(table, 8)) return fail(NH_ERR_ALIGNMENT, "probe_random_red: table must be 8-byte aligned");
+    NH_CUDA(launch_probe_random_red(table, n_entries, n_ops, n_done, S(stream)), "probe_random_red");
+    return NH_OK;
+}
+
 extern "C" nh_status volume_mse(const float* a, const float* b, int64_t n, double* out_dev, void* ws,
                                 size_t ws_bytes, void* stream) {
     if (!a || !b || !out_dev || !ws) return fail(NH_ERR_INVALID_ARG, "volume_mse: null argument");

@@ -125,6 +125,44 @@ cudaError_t launch_sample_rays(const ViewArgs& va, const int32_t* pix, int R, in
     return cudaGetLastError();
 }
 
+// Scatter stage alone: grads[l][idx_k][f] += w_k dh[p][l F + f] for n points, one
+// point per lane, warps over 32 consecutive points (the layout of the training
+// kernels' samples along a ray). Each lane stages its dL/dh row in shared memory in
+// the XOR-swizzled order scatter_point reads.
+template <int D>
+__global__ void __launch_bounds__(128) k_scatter_points(FieldArgs fa, int n, const float* __restrict__ xyz,
+                                                        const float* __restrict__ dh) {
+    __shared__ __align__(16) float rows[4][32][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* row = rows[warp][lane];
+    const long long ntask = ((long long)n + 31) / 32;
+    for (long long task = (long long)blockIdx.x * 4 + warp; task < ntask; task += (long long)gridDim.x * 4) {
+        const long long p = task * 32 + lane;
+        const bool active = p < n;
+        const long long pc = active ? p : (long long)n - 1;
+        const float x[3] = {xyz[3 * pc], xyz[3 * pc + 1], xyz[3 * pc + 2]};
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < D; k += 4) {
+            const float4 v = *reinterpret_cast<const float4*>(dh + pc * D + k);
+            row[k ^ lane] = active ? v.x : 0.f;
+            row[(k + 1) ^ lane] = active ? v.y : 0.f;
+            row[(k + 2) ^ lane] = active ? v.z : 0.f;
+            row[(k + 3) ^ lane] = active ? v.w : 0.f;
+        }
+        __syncwarp();
+        scatter_point<D / 2>(fa, x, row, lane);
+    }
+}
+
+cudaError_t launch_scatter_points(const FieldArgs& fa, int n, const float* xyz, const float* dh, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    long long blocks = ((long long)n + 127) / 128;
+    if (blocks > (long long)num_sms() * 16) blocks = (long long)num_sms() * 16;
+    NH_DISPATCH_D(fa, { k_scatter_points<D_><<<(unsigned)blocks, 128, 0, st>>>(fa, n, xyz, dh); });
+    return cudaGetLastError();
+}
+
 cudaError_t launch_hash_corners(const FieldArgs& fa, int n, const float* xyz, uint32_t* idx, float* w,
                                 cudaStream_t st) {
     if (n == 0) return cudaSuccess;

@@ -88,6 +88,14 @@ cudaError_t launch_hash_corners(const FieldArgs& fa, int n, const float* xyz, ui
 cudaError_t launch_encode_points(const FieldArgs& fa, int n, const float* xyz, float* h,
                                  cudaStream_t st);
 cudaError_t launch_query_volume(const FieldArgs& fa, int D, float* out, cudaStream_t st);
+cudaError_t launch_scatter_points(const FieldArgs& fa, int n, const float* xyz, const float* dh,
+                                  cudaStream_t st);
+// roofline probes (nh_probe.cu)
+cudaError_t launch_probe_l2_read(const void* buf, size_t bytes, int reps, float* sink, cudaStream_t st);
+cudaError_t launch_probe_random_gather(const void* table, size_t n_entries, int entry_bytes, int64_t n_loads,
+                                       float* sink, int64_t* n_done, cudaStream_t st);
+cudaError_t launch_probe_random_red(float* table, size_t n_entries, int64_t n_ops, int64_t* n_done,
+                                    cudaStream_t st);
 size_t      mse_workspace_bytes();
 // sms, occupancy (CTAs/SM by registers and shared memory), CTAs/SM by TMEM, grid,
 // TMEM columns per CTA, dynamic shared memory bytes of the last training launch

@@ -104,6 +104,10 @@ _SIGS = {
     "sample_rays": (_I, [_P, _I, _I, _P, _I, _P, _P, _P]),
     "hash_corners": (_I, [_P, _I, _P, _P, _P, _P]),
     "encode_points": (_I, [_P, _I, _P, _P, _P]),
+    "scatter_points": (_I, [_P, _I, _P, _P, _P]),
+    "probe_l2_read": (_I, [_P, C.c_uint64, _I, _P, _P]),
+    "probe_random_gather": (_I, [_P, C.c_uint64, _I, C.c_int64, _P, C.POINTER(C.c_int64), _P]),
+    "probe_random_red": (_I, [_P, C.c_uint64, C.c_int64, C.POINTER(C.c_int64), _P]),
 }
 EXPORTS = tuple(_SIGS)
 
@@ -431,6 +435,37 @@ def encode_points(field, xyz, h_out, stream=None):
     xyz = _dev(xyz, torch.float32, "xyz")
     _check(load().encode_points(field.handle, xyz.numel() // 3, _ptr(xyz), _ptr(h_out), _stream(stream)),
            "encode_points")
+
+
+def scatter_points(field, xyz, dh, stream=None):
+    """Adds the trilinear scatter of dh (float[n][L F]) at xyz into field.grads."""
+    xyz = _dev(xyz, torch.float32, "xyz")
+    dh = _dev(dh, torch.float32, "dh")
+    _check(load().scatter_points(field.handle, xyz.numel() // 3, _ptr(xyz), _ptr(dh), _stream(stream)),
+           "scatter_points")
+
+
+# ---------------------------------------------------------------------------- roofline probes
+def probe_l2_read(buf, reps, sink, stream=None):
+    _check(load().probe_l2_read(_ptr(buf), buf.numel() * buf.element_size(), int(reps), _ptr(sink),
+                                _stream(stream)), "probe_l2_read")
+
+
+def probe_random_gather(table, entry_bytes, n_loads, sink, stream=None):
+    """Random entry_bytes loads from table (n_entries = bytes / entry_bytes); returns the count issued."""
+    done = C.c_int64()
+    n_entries = table.numel() * table.element_size() // entry_bytes
+    _check(load().probe_random_gather(_ptr(table), n_entries, int(entry_bytes), int(n_loads), _ptr(sink),
+                                      C.byref(done), _stream(stream)), "probe_random_gather")
+    return done.value
+
+
+def probe_random_red(table, n_ops, stream=None):
+    """Random float2 atomic adds into table (float32, even length); returns the count issued."""
+    done = C.c_int64()
+    _check(load().probe_random_red(_ptr(table), table.numel() // 2, int(n_ops), C.byref(done), _stream(stream)),
+           "probe_random_red")
+    return done.value
 
 
 # ---------------------------------------------------------------------------- autograd
