@@ -69,47 +69,93 @@ def parse_args():
 
 
 # ------------------------------------------------------------------------------ CPU oracle
-def oracle_sample_rays(w: S.Workload, seconds: float, seed: int):
-    """Oracle train steps on bounded batches (same field shape, N and geometry)
-    until about ``seconds`` of work; returns (samples, seconds, description)."""
+ORACLE_RAYS = 16          # rays per bounded oracle batch
+
+
+def _oracle_worker(args):
+    """One CPU worker: oracle forward + loss + backward (Sec. 2.5) on bounded batches of
+    ORACLE_RAYS rays for about `seconds`, then one dense Adam update of its 1/n_share
+    of the parameters. Returns (rays, seconds of ray work, seconds of Adam)."""
+    name, seconds, seed, share, n_share = args
     import oracle
+    w = S.WORKLOADS[name]
     g, f = w.geometry, w.field
     tab, du, dv = oracle.view_table(g.n_views, g.angle0_rad, g.span_rad, g.dso_mm, g.dsd_mm,
                                     g.det_du_mm, g.det_dv_mm, g.vol_side_mm)
     og = (tab, du, dv, g.det_nu, g.det_nv)
     rng = np.random.default_rng(seed)
-    flat = S.init_params(f, seed).astype(np.float64)
-    st = oracle.AdamState.zeros(flat.size)
-    R = 16
-    samples, t0, steps = 0, time.perf_counter(), 0
-    while True:
+    flat = S.init_params(f, 0).astype(np.float64)
+    rays, t_rays = 0, 0.0
+    grad = None
+    while t_rays < seconds:
         view = int(rng.integers(0, g.n_views))
-        _, _, _, _, hit = oracle.ray_setup(tab, du, dv, g.det_nu, g.det_nv, view,
-                                           np.arange(g.det_nu * g.det_nv))
-        pix = rng.choice(np.nonzero(hit)[0], size=R, replace=False).astype(np.int32)
-        a_meas = rng.uniform(0, 1, size=R).astype(np.float32)
-        flat, st, _, _ = oracle.train_step(flat, st, f, og, view, pix, a_meas, w.n_samples)
-        samples += R * w.n_samples
-        steps += 1
-        el = time.perf_counter() - t0
-        if el >= seconds:
-            break
-    desc = (f"{steps} oracle train steps of {R} rays x {w.n_samples} samples on the {w.name} field "
-            f"(T=2^{f.log2_T}, L={f.n_levels}, dense Adam over all {flat.size} parameters), float64 numpy")
-    return samples, el, desc
+        _, _, _, _, hit = oracle.ray_setup(tab, du, dv, g.det_nu, g.det_nv, view, np.arange(g.det_nu * g.det_nv))
+        pix = rng.choice(np.nonzero(hit)[0], size=ORACLE_RAYS, replace=False).astype(np.int32)
+        a_meas = rng.uniform(0, 1, size=ORACLE_RAYS).astype(np.float32)
+        t0 = time.perf_counter()
+        A, cache = oracle.render_forward(flat, f, og, view, pix, w.n_samples)
+        _, dLdA = oracle.loss_and_grad(A, a_meas, f.loss)
+        grad = oracle.render_backward(cache, dLdA, f)
+        t_rays += time.perf_counter() - t0
+        rays += ORACLE_RAYS
+    lo, hi = flat.size * share // n_share, flat.size * (share + 1) // n_share
+    st = oracle.AdamState(np.zeros(hi - lo), np.zeros(hi - lo), 0)
+    t0 = time.perf_counter()
+    oracle.adam_step(flat[lo:hi], grad[lo:hi], st, f)
+    return rays, t_rays, time.perf_counter() - t0
+
+
+class OraclePool:
+    """The CPU oracle on `workers` host cores (spawned processes, one BLAS thread each).
+    A measurement scales the bounded sample to a full step of the workload: the ray
+    work's rate summed over the cores gives R rays' time, plus the slowest core's
+    share of the dense Adam update."""
+
+    def __init__(self, workers: int):
+        import multiprocessing as mp
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[v] = "1"
+        self.workers = workers
+        self.pool = mp.get_context("spawn").Pool(workers)
+
+    def measure(self, w: S.Workload, seconds: float, seed: int):
+        res = self.pool.map(_oracle_worker, [(w.name, seconds, seed * 1000 + k, k, self.workers)
+                                             for k in range(self.workers)])
+        ray_rate = sum(r[0] / r[1] for r in res)
+        t_adam = max(r[2] for r in res)
+        step_s = w.n_rays / ray_rate + t_adam
+        rays = sum(r[0] for r in res)
+        f = w.field
+        desc = (f"{rays} rays x {w.n_samples} samples of oracle forward+loss+backward in batches of "
+                f"{ORACLE_RAYS} on the {w.name} field (L={f.n_levels}, T=2^{f.log2_T}) over {self.workers} "
+                f"cores, plus a dense Adam over all {S.param_layout(f)['_total'][1]} parameters split "
+                f"across the cores, scaled to one {w.n_rays}-ray step ({step_s:.3f} s), float64 numpy")
+        return w.n_rays * w.n_samples / step_s, step_s, desc
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 def cpu_baseline(w: S.Workload, seconds: float, seed: int):
-    """Runs the oracle in a fresh single-threaded interpreter (BLAS pinned to 1 thread)."""
+    """Runs the oracle on every host core in a fresh interpreter that never touches
+    the GPU (CUDA_VISIBLE_DEVICES empty)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", "--workload", w.name,
            "--cpu-seconds", str(seconds), "--seed", str(seed)]
-    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=seconds * 10 + 120)
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=seconds * 20 + 300)
     if r.returncode != 0:
-        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": r.stderr[-300:]}
+        return {"value": None, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "error": r.stderr[-300:]}
     out = json.loads(r.stdout.strip().splitlines()[-1])
-    return {"value": out["value"], "unit": UNIT, "cores": 1, "kind": "oracle", "sample": out["sample"]}
+    return {"value": out["value"], "unit": UNIT, "cores": out["cores"], "kind": "oracle", "sample": out["sample"]}
 
 
 # ------------------------------------------------------------------------------ GPU helpers
@@ -602,26 +648,26 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
 
 def run_reference(args, rank: int, world: int):
+    """The CPU oracle as the reference arm: each step is one bounded sample of the
+    workload on every host core, scaled to a full step (OraclePool)."""
     if rank != 0:
         return
     w = S.WORKLOADS[args.workload]
-    # one bounded oracle sample per step: about 2 s each keeps K + W steps within minutes
+    pool = OraclePool(cpu_cores())
     per_step = 2.0
-    for _ in range(args.warmup):
-        oracle_sample_rays(w, 0.1, args.seed)
-    t0 = time.perf_counter()
-    samples = 0.0
-    desc = ""
+    for k in range(args.warmup):
+        pool.measure(w, 0.2, args.seed + 100 + k)
+    total_s, desc = 0.0, ""
     for k in range(args.steps):
-        n, _, desc = oracle_sample_rays(w, per_step, args.seed + k)
-        samples += n
-    el = time.perf_counter() - t0
-    value = samples / el
+        _, step_s, desc = pool.measure(w, per_step, args.seed + k)
+        total_s += step_s
+    pool.close()
+    value = w.n_rays * w.n_samples * args.steps / total_s
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": w.name, "rays_per_step": w.n_rays, "samples_per_ray": w.n_samples},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.workers, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -629,8 +675,10 @@ def run_reference(args, rank: int, world: int):
 def main():
     args = parse_args()
     if args.cpu_worker:
-        n, el, desc = oracle_sample_rays(S.WORKLOADS[args.workload], args.cpu_seconds, args.seed)
-        print(json.dumps({"value": n / el, "sample": desc}))
+        pool = OraclePool(cpu_cores())
+        value, _, desc = pool.measure(S.WORKLOADS[args.workload], args.cpu_seconds, args.seed)
+        pool.close()
+        print(json.dumps({"value": value, "sample": desc, "cores": pool.workers}))
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

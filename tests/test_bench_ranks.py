@@ -72,4 +72,4 @@ def test_reference_arm_prints_only_on_rank_zero():
                        timeout=300)
     assert r.returncode == 0
     line = json.loads(r.stdout.strip().splitlines()[-1])
-    assert line["impl"] == "reference" and line["value"] > 0 and line["cpu_baseline"]["cores"] == 1
+    assert line["impl"] == "reference" and line["value"] > 0 and line["cpu_baseline"]["cores"] >= 1
