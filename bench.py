@@ -58,7 +58,9 @@ def parse_args():
     p.add_argument("--no-psnr", action="store_true", help="skip the time-to-PSNR runs")
     p.add_argument("--no-l2", action="store_true", help="skip the gather / scatter L2 roofline probes")
     p.add_argument("--psnr-steps", type=int, default=3000, help="step cap of the time-to-PSNR runs")
-    p.add_argument("--experiment", default="", choices=["", "mci"])
+    p.add_argument("--experiment", default="", choices=["", "mci", "fftmask"])
+    p.add_argument("--mask-step", type=int, default=500, help="fftmask: step at which the mask is chosen")
+    p.add_argument("--mask-grid", type=int, default=64, help="fftmask: voxel grid of the feature spectra")
     p.add_argument("--mci-cases", type=int, default=8)
     p.add_argument("--mci-heldout", type=int, default=8)
     p.add_argument("--mci-recon-steps", type=int, default=1500)
@@ -459,6 +461,47 @@ def l2_roofline(nh, torch, geom, fields, batch, N, dev):
     return out
 
 
+def run_fftmask(args):
+    """FFT channel masking (Sec. 2.3) on the benchmark scan: the same initialisation
+    and batches trained with no mask, and with the mask chosen from the hash
+    features' spectra after --mask-step steps (channel_mask.select_channel_mask),
+    to --psnr-steps steps; PSNR every 50 steps (evaluation not timed)."""
+    import torch
+    from paper_2506_19742_gb300 import build as nhbuild
+    from paper_2506_19742_gb300 import channel_mask as cm
+    from paper_2506_19742_gb300 import nhcbct as nh
+    from paper_2506_19742_gb300 import recon
+    nhbuild.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    w = S.WORKLOADS[args.workload]
+    geom, vol, a_meas_all, cands = make_scan(nh, torch, w, args.seed, dev)
+    vol_gt = torch.from_numpy(vol.astype(np.float32).ravel()).to(dev)
+    out = {"experiment": "fftmask", "workload": w.name, "mask_step": args.mask_step, "steps": args.psnr_steps,
+           "grid": args.mask_grid, "cutoff": 0.25, "threshold": 0.85}
+    for arm in ("none", "fft"):
+        rec = recon.Reconstruction(w.field, geom, params=S.init_params(w.field, args.seed))
+        it = device_batches(torch, w, cands, a_meas_all, 500, args.seed + 5, dev)
+        curve, reached = [], {}
+        for s in range(1, args.psnr_steps + 1):
+            view, pix, a = next(it)
+            rec.step(view, pix, a, w.n_samples)
+            if arm == "fft" and s == args.mask_step:
+                mask, frac = cm.select_channel_mask(rec.field, G=args.mask_grid)
+                out["mask"] = mask.astype(int).tolist()
+                out["high_frequency_fraction"] = [round(float(x), 3) for x in frac]
+            if s % 50 == 0:
+                p = rec.psnr(vol_gt)
+                curve.append((s, round(p, 3)))
+                for t in (25.0, 30.0, 35.0):
+                    if t not in reached and p >= t:
+                        reached[t] = s
+        out[arm] = {"final_psnr": curve[-1][1], "best_psnr": max(c[1] for c in curve),
+                    "steps_to": {str(t): reached.get(t) for t in (25.0, 30.0, 35.0)},
+                    "psnr_at": curve[:: max(1, len(curve) // 12)]}
+    print(json.dumps(out))
+
+
 def run_ours(args, rank: int, world: int, local_rank: int):
     import torch
     from paper_2506_19742_gb300 import build as nhbuild
@@ -686,6 +729,9 @@ def main():
     if args.experiment == "mci":
         if rank == 0:
             run_mci(args)
+    elif args.experiment == "fftmask":
+        if rank == 0:
+            run_fftmask(args)
     elif args.impl == "reference":
         run_reference(args, rank, world)
     else:

@@ -18,7 +18,9 @@ imports it; both sides receive the same seeded inputs from ``synthetic``.
 Parity status: every function here is pinned by a ``-m "not gpu"`` test against
 a closed form, a library routine, brute force or finite differences, except the
 transfer *gain* of Mapping Consistency Initialization, which has no closed form
-(parity unpinned; it is measured against random initialization instead).
+(parity unpinned; it is measured against random initialization instead). The FFT
+channel mask (mask.py) is pinned on pure tones, white noise and planted fields;
+the paper gives no grid, statistic or threshold, so those are a stated reading.
 """
 from .geometry import view_table, ray_setup, sample_points, voxel_centres_f32
 from .encoding import level_resolutions, corners, encode, encode_backward
@@ -27,6 +29,7 @@ from .field import (unflatten, flatten, normalize_forward, normalize_backward,
 from .train import (render, loss_and_grad, render_forward, render_backward, adam_step,
                     train_step, fit_points_step, query_points, query_volume, AdamState)
 from .project import project
+from .mask import radial_frequency, high_frequency_fraction, mask_from_fraction, channel_mask
 
 __all__ = [
     "view_table", "ray_setup", "sample_points", "voxel_centres_f32",
@@ -35,5 +38,5 @@ __all__ = [
     "mlp_forward", "mlp_backward", "field_forward", "field_backward",
     "render", "loss_and_grad", "render_forward", "render_backward", "adam_step",
     "train_step", "fit_points_step", "query_points", "query_volume", "AdamState",
-    "project",
+    "project", "radial_frequency", "high_frequency_fraction", "mask_from_fraction", "channel_mask",
 ]

@@ -689,7 +689,7 @@ k_ray_backward(FieldArgs fa, ViewArgs va, const int32_t* __restrict__ pix, int R
 // tensor memory; the CTA sums each ray's chunks in order into A_r (Eq. 1), forms the
 // loss term and dL/dA_r (MSE or L1, Eq. 3) in shared memory, and every warp carries
 // on with the backward of the same samples. Ray-tile losses are accumulated in ray
-// order per CTA; k_train_loss adds the CTA partials in order.
+// order per CTA; k_train_loss adds the CTA partials in a fixed order.
 template <int D, int G, typename TT>
 struct TrainCarry {
     using type = FfmaCarry<D, G>;
@@ -780,12 +780,20 @@ k_ray_train(FieldArgs fa, ViewArgs va, const int32_t* __restrict__ pix, const fl
     if (threadIdx.x == 0) loss_part[blockIdx.x] = s_loss;
 }
 
-// loss = (sum of CTA partials in order) / R.
+// Sum of n CTA partials in a fixed order with one warp: lane t adds partials
+// t, t + 32, ... in turn, then a fixed butterfly combines the lane sums (lane 0's
+// result is used), so the loss is the same on every run.
+__device__ __forceinline__ float ordered_partial_sum(const float* __restrict__ part, int n, int lane) {
+    float s = 0.f;
+    for (int k = lane; k < n; k += 32) s += part[k];
+    return warp_sum(s);
+}
+
+// loss = (ordered sum of the CTA partials) / R.
 static __global__ void k_train_loss(const float* __restrict__ part, int n_part, int R, float* loss_out,
                                     DeviceState* state) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    float s = 0.f;
-    for (int k = 0; k < n_part; k++) s += part[k];
+    const float s = ordered_partial_sum(part, n_part, threadIdx.x);
+    if (threadIdx.x != 0) return;
     const float loss = s / (float)R;
     if (loss_out) *loss_out = loss;
     if (!isfinite(loss)) atomicOr(&state->flags, NH_FLAG_NONFINITE);
@@ -851,10 +859,9 @@ k_points_fit(FieldArgs fa, int n, const float* __restrict__ xyz, const float* __
 }
 
 static __global__ void k_points_loss(const float* __restrict__ part, int n_part, int n, float* loss_out,
-                              DeviceState* state) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    float s = 0.f;
-    for (int k = 0; k < n_part; k++) s += part[k];
+                                     DeviceState* state) {
+    const float s = ordered_partial_sum(part, n_part, threadIdx.x);
+    if (threadIdx.x != 0) return;
     const float loss = s / (float)n;
     if (loss_out) *loss_out = loss;
     if (!isfinite(loss)) atomicOr(&state->flags, NH_FLAG_NONFINITE);

@@ -574,3 +574,36 @@ def test_full_size_sampled_rays_match_oracle(lib, wname):
             _grad_close(_np(field.flat_grads()), g_ref, cfg, what=f"{wname} ray {r}")
         else:
             _grad_close(_np(field.flat_grads()), g_ref, cfg, what=f"{wname} ray {r}", norm_rtol=tol_g)
+
+
+# ------------------------------------------------------------------------------ FFT channel mask
+def test_fft_channel_mask_matches_oracle(lib):
+    """The channel mask chosen from the library's gather on the GPU (Sec. 2.3) equals
+    the oracle's, on a planted field (a smooth dense level, constant levels, a
+    white-noise hashed level) and on a randomly initialised 16-level field."""
+    from paper_2506_19742_gb300 import channel_mask as cm
+    cfg = S.FieldConfig(n_levels=8, n_feat=2, log2_T=10, base_res=4, max_res=512, norm=S.NORM_LN,
+                        hidden_layers=1, width=32)
+    assert oracle.level_resolutions(8, 4, 512)[0] == 4
+    flat = S.init_params(cfg, 0).astype(np.float32)
+    T = cfg.T
+    tab = np.zeros((8, T, 2), dtype=np.float32)   # levels 1..6 constant (no variance: kept)
+    for zz in range(5):
+        for yy in range(5):
+            for xx in range(5):
+                tab[0, xx + 5 * yy + 25 * zz] = [0.3 * xx - 0.1 * zz, 0.2 * yy]
+    tab[7] = np.random.default_rng(1).normal(size=(T, 2))
+    flat[: 8 * T * 2] = tab.ravel()
+    cases = [(cfg, flat, 32), (field_cfg(n_levels=16, log2_T=12, base_res=16, max_res=512),
+                               S.init_params(field_cfg(n_levels=16, log2_T=12, base_res=16, max_res=512), 3,
+                                             table_scale=0.5), 24)]
+    masks = []
+    for c, f, G in cases:
+        field = lib.Field(c, params=f)
+        mask, frac = cm.select_channel_mask(field, G=G, cutoff=0.25, threshold=0.85)
+        ref_mask, ref_frac = oracle.channel_mask(f.astype(np.float64), c, G=G, cutoff=0.25, threshold=0.85)
+        np.testing.assert_allclose(frac, ref_frac, rtol=0, atol=1e-5)
+        clear = np.abs(ref_frac - 0.85) > 1e-4            # decisions float32 rounding cannot flip
+        assert np.array_equal(mask[clear], ref_mask[clear].astype(np.float32)), (frac, ref_frac)
+        masks.append(mask)
+    np.testing.assert_array_equal(masks[0], [1] * 14 + [0, 0])

@@ -431,3 +431,43 @@ def test_projector_of_uniform_volume_is_chord_less_boundary_ramp():
         centre = (nv // 2) * nu + nu // 2
         axis = int(np.argmax(ad[centre]))
         assert abs(loss[centre] - 1.0 / (4 * D * ad[centre, axis])) < 2e-4
+
+
+# ---------------------------------------------------------------- FFT channel masking (Sec. 2.3)
+def test_fft_high_frequency_fraction_of_tones_constants_and_white_noise():
+    """Pure tones put all their power at one radius |k| = |n| / G, a constant has
+    none, and white noise spreads it evenly over the G^3 - 1 non-zero bins."""
+    G = 16
+    z, y, x = np.meshgrid(np.arange(G), np.arange(G), np.arange(G), indexing="ij")
+    noise = np.random.default_rng(0).normal(size=(G, G, G))
+    chans = [np.cos(2 * np.pi * 2 * x / G),            # |k| = 0.125
+             np.cos(2 * np.pi * 6 * y / G),            # |k| = 0.375
+             np.sin(2 * np.pi * (3 * x + 3 * z) / G),  # |k| = 3 sqrt(2) / 16 = 0.265
+             np.full((G, G, G), 0.7), noise]
+    h = np.stack(chans, axis=-1).reshape(G ** 3, -1)
+    frac = oracle.high_frequency_fraction(h, G, 0.25)
+    np.testing.assert_allclose(frac[:4], [0.0, 1.0, 1.0, 0.0], atol=1e-12)
+    n_high = sum(1 for a in range(-G // 2, G // 2) for b in range(-G // 2, G // 2)
+                 for c in range(-G // 2, G // 2) if (a * a + b * b + c * c) > (0.25 * G) ** 2)
+    assert abs(frac[4] - n_high / (G ** 3 - 1)) < 0.03
+    np.testing.assert_array_equal(oracle.mask_from_fraction(frac, 0.85), [1, 0, 0, 1, 0])
+
+
+def test_channel_mask_keeps_a_smooth_dense_level_and_drops_a_hashed_noise_level():
+    """Level 0 (dense, N = 4) holds a linear function of the vertex coordinates, so
+    its features vary smoothly; level 1 (hashed, N = 512) holds independent random
+    entries, which a 32^3 grid samples as white noise."""
+    cfg = S.FieldConfig(n_levels=2, n_feat=2, log2_T=10, base_res=4, max_res=512, norm=S.NORM_LN,
+                        hidden_layers=1, width=32)
+    flat = S.init_params(cfg, 0).astype(np.float64)
+    T = cfg.T
+    tab = np.zeros((2, T, 2))
+    for zz in range(5):
+        for yy in range(5):
+            for xx in range(5):
+                tab[0, xx + 5 * yy + 25 * zz] = [0.3 * xx - 0.1 * zz, 0.2 * yy]
+    tab[1] = np.random.default_rng(1).normal(size=(T, 2))
+    flat[: 2 * T * 2] = tab.ravel()
+    mask, frac = oracle.channel_mask(flat, cfg, G=32, cutoff=0.25, threshold=0.85)
+    np.testing.assert_array_equal(mask, [1, 1, 0, 0])
+    assert frac[:2].max() < 0.1 and frac[2:].min() > 0.85
