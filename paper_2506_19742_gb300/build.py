@@ -15,9 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnhcbct.so")
-SOURCES = ["nh_api.cu", "nh_field.cu", "nh_field_f32.cu", "nh_field_bf16.cu", "nh_field_f16.cu",
-           "nh_adam.cu", "nh_project.cu",
-           "nh_probe.cu"]
+SOURCES = ["nh_train_f32.cu", "nh_train_bf16.cu", "nh_train_f16.cu", "nh_field_f32.cu", "nh_field_bf16.cu",
+           "nh_field_f16.cu", "nh_api.cu", "nh_field.cu", "nh_adam.cu", "nh_project.cu", "nh_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

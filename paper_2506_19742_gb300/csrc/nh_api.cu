@@ -427,7 +427,7 @@ static nh_status run_accumulate(nh_field* f, const nh_geometry* g, int view, int
                                 const float* a_meas, int N, float* loss_dev, const RayWs& w, cudaStream_t st) {
     const ViewArgs va = view_args(g, view);
     const int C = (N + 31) / 32;
-    if (C <= 8) {   // whole rays fit a CTA: one fused forward + loss + backward kernel
+    if (C <= kMaxFusedChunks) {   // whole rays fit a CTA: one fused forward + loss + backward kernel
         NH_CUDA(launch_ray_train(f->fa, va, pix, a_meas, R, N, f->desc.loss, w.loss_part, loss_dev, st),
                 "train_step fused");
     } else {

@@ -257,6 +257,7 @@ static __global__ void __launch_bounds__(1024) k_ray_loss(const float* __restric
 constexpr int kStage = 32 * (kW + 1);
 __host__ __device__ constexpr int warp_scratch_floats() { return kStage + 32 * kW; }
 constexpr int kBwdWarps = 8;
+constexpr int kMaxTrainWarps = kMaxFusedChunks;
 
 __device__ __forceinline__ int swz(int s, int j) {   // column j of dz row s
     return s * kW + ((((j >> 2) ^ (s & 7)) << 2) | (j & 3));
@@ -565,8 +566,8 @@ __host__ __device__ inline int bwd_cols_per_thread(int precision, int H) {
     return precision == NH_PREC_F32 ? 32 * H : mma_tmem_cols_per_thread(H) + 32;
 }
 // TMEM columns per CTA: two lane-quarter groups of warps, rounded to a power of two.
-static uint32_t bwd_tmem_cols(const FieldArgs& fa) {
-    uint32_t need = (uint32_t)(kBwdWarps / 4) * (uint32_t)bwd_cols_per_thread(fa.precision, fa.H), c = 32;
+static uint32_t bwd_tmem_cols(const FieldArgs& fa, int nwarps = kBwdWarps) {
+    uint32_t need = (uint32_t)((nwarps + 3) / 4) * (uint32_t)bwd_cols_per_thread(fa.precision, fa.H), c = 32;
     while (c < need) c <<= 1;
     return c;
 }
@@ -581,11 +582,11 @@ __host__ __device__ inline int bwd_warp_floats(int precision) {
     return precision == NH_PREC_F32 ? warp_scratch_floats() : kMmaWarpFloats;
 }
 
-static size_t bwd_smem_bytes(const FieldArgs& fa) {
+static size_t bwd_smem_bytes(const FieldArgs& fa, int nwarps = kBwdWarps) {
     const int ndp = (fa.n_dense + 3) & ~3;
-    size_t b = (size_t)(2 * ndp + kMaxD + kBwdWarps * bwd_warp_floats(fa.precision)) * sizeof(float);
+    size_t b = (size_t)(2 * ndp + kMaxD + nwarps * bwd_warp_floats(fa.precision)) * sizeof(float);
     if (fa.precision != NH_PREC_F32) b += (size_t)fa.H * kMmaLayerElems * 2;
-    if (512u / bwd_tmem_cols(fa) < 2u && b < 120 * 1024) b = 120 * 1024;
+    if (512u / bwd_tmem_cols(fa, nwarps) < 2u && b < 120 * 1024) b = 120 * 1024;
     return b;
 }
 
@@ -606,7 +607,7 @@ __device__ __forceinline__ BwdCta bwd_begin(const FieldArgs& fa, float* smem, ui
     c.sg = c.smask + kMaxD;
     const int wf = bwd_warp_floats(fa.precision);
     c.wbuf = c.sg + ndp + warp * wf;
-    uint16_t* sw = reinterpret_cast<uint16_t*>(c.sg + ndp + kBwdWarps * wf);
+    uint16_t* sw = reinterpret_cast<uint16_t*>(c.sg + ndp + (int)(blockDim.x >> 5) * wf);
     c.sw = sw;
     if (warp == 0) tmem_alloc(s_tmem, tcols);
     load_dense(fa, c.sp, c.smask);
@@ -705,18 +706,19 @@ struct TrainCarry<D, G, __half> {
     using type = MmaCarry<D, G>;
 };
 
-// NW: most warps a CTA launches with; CTAs of at most six warps (rays of three,
+// NW: most warps a CTA launches with. CTAs of at most six warps (rays of three,
 // five or six chunks) are compiled with the register budget of two six-warp CTAs
-// per SM instead of two eight-warp ones.
+// per SM instead of two eight-warp ones; CTAs of 9..16 warps (one long ray each)
+// run one per SM.
 template <int D, int G, typename TT, int NW>
-__global__ void __launch_bounds__(NW * 32, 2)
+__global__ void __launch_bounds__(NW * 32, NW > 8 ? 1 : 2)
 k_ray_train(FieldArgs fa, ViewArgs va, const int32_t* __restrict__ pix, const float* __restrict__ a_meas, int R,
             int N, int C, int rpr, int loss_kind, float* __restrict__ loss_part, uint32_t tcols) {
     extern __shared__ __align__(16) float smem[];
     __shared__ uint32_t s_tmem;
-    __shared__ float s_part[kBwdWarps];
-    __shared__ float s_g[kBwdWarps];
-    __shared__ float s_lr[kBwdWarps];
+    __shared__ float s_part[kMaxTrainWarps];
+    __shared__ float s_g[kMaxTrainWarps];
+    __shared__ float s_lr[kMaxTrainWarps];
     __shared__ float s_loss;
     const BwdCta cta = bwd_begin<TT>(fa, smem, &s_tmem, tcols);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1132,25 +1134,30 @@ cudaError_t launch_query_volume_tt(const FieldArgs& fa, int D, float* out, cudaS
     return cudaGetLastError();
 }
 
-// Fused training step (k_ray_train) when a ray has at most kBwdWarps chunks of 32
-// samples; returns cudaErrorNotSupported otherwise (the caller then runs forward,
-// loss and backward as separate kernels). loss_part: >= 4096 floats of workspace.
+// Fused training step (k_ray_train) when a ray has at most kMaxFusedChunks chunks of
+// 32 samples; returns cudaErrorNotSupported otherwise (the caller then runs forward,
+// loss and backward as separate kernels). Rays of up to 8 chunks are packed
+// 8 / C to a CTA of C * (8 / C) warps, two CTAs per SM; longer rays take one CTA of C
+// warps each, one CTA per SM (its TMEM groups fill the SM's 512 columns).
+// loss_part: >= kTrainParts floats of workspace.
 template <typename TT>
 cudaError_t launch_ray_train_tt(const FieldArgs& fa, const ViewArgs& va, const int32_t* pix, const float* a_meas,
                                 int R, int N, int loss_kind, float* loss_part, float* loss_out, cudaStream_t st) {
     const int C = (N + 31) / 32;
-    if (C > kBwdWarps || R <= 0) return cudaErrorNotSupported;
-    const int rpr = kBwdWarps / C;
-    const int threads = rpr * C * 32;
+    if (C > kMaxFusedChunks || R <= 0) return cudaErrorNotSupported;
+    const int rpr = C <= kBwdWarps ? kBwdWarps / C : 1;
+    const int nw = rpr * C;
+    const int threads = nw * 32;
     const long long ngroups = ((long long)R + rpr - 1) / rpr;
-    const size_t sm = bwd_smem_bytes(fa);
-    const uint32_t tcols = bwd_tmem_cols(fa);
+    const size_t sm = bwd_smem_bytes(fa, nw);
+    const uint32_t tcols = bwd_tmem_cols(fa, nw);
     NH_DISPATCH_DG(fa, {
-        auto k = threads <= 6 * 32 ? k_ray_train<D_, G_, TT, 6> : k_ray_train<D_, G_, TT, kBwdWarps>;
+        auto k = nw <= 6 ? k_ray_train<D_, G_, TT, 6>
+                         : (nw <= kBwdWarps ? k_ray_train<D_, G_, TT, kBwdWarps> : k_ray_train<D_, G_, TT, kMaxTrainWarps>);
         cudaError_t e = set_smem(k, sm);
         if (e != cudaSuccess) return e;
         long long blocks = train_grid(k, sm, tcols, ngroups, threads);
-        if (blocks > 4096) blocks = 4096;
+        if (blocks > kTrainParts) blocks = kTrainParts;
         k<<<(unsigned)blocks, threads, sm, st>>>(fa, va, pix, a_meas, R, N, C, rpr, loss_kind, loss_part, tcols);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -1159,9 +1166,14 @@ cudaError_t launch_ray_train_tt(const FieldArgs& fa, const ViewArgs& va, const i
     return cudaGetLastError();
 }
 
-#define NH_INSTANTIATE_FIELD(TT)                                                                            \
+// The fused training launcher is instantiated in its own translation units
+// (nh_train_*.cu) and the rest in nh_field_*.cu, so the build compiles them in
+// parallel.
+#define NH_INSTANTIATE_TRAIN(TT)                                                                            \
     template cudaError_t launch_ray_train_tt<TT>(const FieldArgs&, const ViewArgs&, const int32_t*, const float*, \
-                                                 int, int, int, float*, float*, cudaStream_t);              \
+                                                 int, int, int, float*, float*, cudaStream_t);
+
+#define NH_INSTANTIATE_FIELD(TT)                                                                            \
     template cudaError_t launch_ray_forward_tt<TT>(const FieldArgs&, const ViewArgs&, const int32_t*, int, int, \
                                                    float*, cudaStream_t);                                   \
     template cudaError_t launch_ray_backward_tt<TT>(const FieldArgs&, const ViewArgs&, const int32_t*, int,   \

@@ -66,6 +66,7 @@ cudaError_t launch_ray_backward(const FieldArgs& fa, const ViewArgs& va, const i
 // Fused forward + loss + backward (rays of at most 8 chunks of 32 samples);
 // cudaErrorNotSupported for longer rays. loss_part: >= kTrainParts floats.
 constexpr int kTrainParts = 4096;
+constexpr int kMaxFusedChunks = 16;   // rays of up to 16 x 32 samples take the fused kernel
 cudaError_t launch_ray_train(const FieldArgs& fa, const ViewArgs& va, const int32_t* pix, const float* a_meas,
                              int R, int N, int loss_kind, float* loss_part, float* loss_out, cudaStream_t st);
 // query (mu_gt == null) or MCI fit step (loss written to loss_out, CTA partials in loss_part)

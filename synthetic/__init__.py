@@ -126,6 +126,12 @@ WORKLOADS = {
     # the paper-scale shape in mixed precision (for the mixed-vs-FP32 comparison)
     "paper_bf16": Workload("paper_bf16", 128, 10, True, False, _G50_256,
                            dataclasses.replace(_F_PAPER, precision=PREC_BF16), 2048, 192, 3000),
+    # the paper's own step shape (Sec. 3.1): one view, 1024 rays x 320 samples, the L1
+    # pixel loss of Eq. 3, on the paper-scale field and scan
+    "paper320_fp32": Workload("paper320_fp32", 128, 10, True, False, _G50_256,
+                              dataclasses.replace(_F_PAPER, loss=LOSS_L1), 1024, 320, 3000),
+    "paper320_bf16": Workload("paper320_bf16", 128, 10, True, False, _G50_256,
+                              dataclasses.replace(_F_PAPER, loss=LOSS_L1, precision=PREC_BF16), 1024, 320, 3000),
     # 256^3 with bone-like shells, 100 views of 512^2, T=2^21, 8192 rays x 256 samples, BF16
     "large_bf16": Workload("large_bf16", 256, 20, False, True, _G100_512, _F_LARGE, 8192, 256, 3000),
 }

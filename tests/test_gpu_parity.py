@@ -208,10 +208,11 @@ def test_train_step_loss_and_gradients_match_oracle(lib, case, loss):
 
 
 @pytest.mark.parametrize("precision", [S.PREC_F32, S.PREC_BF16])
-@pytest.mark.parametrize("N", [64, 192, 300])
+@pytest.mark.parametrize("N", [64, 192, 300, 520])
 def test_train_step_fused_and_split_paths_match_oracle(lib, precision, N):
     """train_step runs one fused forward+loss+backward kernel when a ray has at most
-    8 chunks of 32 samples (N <= 256) and separate kernels otherwise (N = 300): both
+    16 chunks of 32 samples (N <= 512: several rays per CTA up to 8 chunks, one ray
+    per CTA for N = 300) and separate kernels otherwise (N = 520): all
     give the oracle's loss, and one step's parameter update agrees with the update the
     oracle's gradient gives."""
     cfg = field_cfg(n_levels=16, hidden_layers=4, log2_T=12, max_res=256, precision=precision,
