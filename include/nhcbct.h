@@ -169,9 +169,15 @@ nh_status field_poll_status(nh_field* f, void* stream, uint32_t* flags, float* l
 
 /* ------------------------------------------------------------------ training
  * A ray batch: one view, n_rays detector pixels (Sec. 3.1: one view per batch,
- * rays per view), n_samples midpoint samples per ray along [near, far] of the
- * ray's intersection with the volume (delta = (far - near) / n_samples). Rays
- * that miss the volume predict A = 0 and contribute no gradient.
+ * rays per view), n_samples samples per ray along [near, far] of the ray's
+ * intersection with the volume ("sample points along the X-ray trajectories",
+ * Sec. 2.1), delta = (far - near) / n_samples. Sample i sits at
+ * t_i = near + (i + u_i) delta: u_i = 1/2 (midpoint rule) when jitter_seed is 0;
+ * otherwise stratified jitter, u_i = (top 24 bits of output number
+ * pix * n_samples + i + 1 of the SplitMix64 generator started at jitter_seed)
+ * * 2^-24, so forward and backward of one batch see the same samples and a new
+ * seed per step draws new ones. Rays that miss the volume predict A = 0 and
+ * contribute no gradient.
  * pix: device int32[n_rays]; a_meas: device float[n_rays] (may be NULL where unused).
  */
 typedef struct {
@@ -180,6 +186,7 @@ typedef struct {
     const int32_t* pix;
     const float*   a_meas;
     int32_t        n_samples;
+    uint64_t       jitter_seed;   /* 0: midpoint samples */
 } nh_ray_batch;
 
 /* Workspace bytes needed by train_step / render_* / fit_points_step for a batch. */
@@ -191,8 +198,8 @@ nh_status train_step(nh_field* f, const nh_geometry* g, const nh_ray_batch* b, f
                      void* ws, size_t ws_bytes, void* stream);
 /* train_step without the optimizer: forward, loss (written to loss_dev[0]) and
  * backward, ACCUMULATING into grads, so that several batches can be accumulated
- * before one optimizer_step. When every ray has at most 8 chunks of 32 samples
- * (n_samples <= 256) this is one fused kernel per call. */
+ * before one optimizer_step. When every ray has at most 16 chunks of 32 samples
+ * (n_samples <= 512) this is one fused kernel per call. */
 nh_status accumulate_step(nh_field* f, const nh_geometry* g, const nh_ray_batch* b, float* loss_dev,
                           void* ws, size_t ws_bytes, void* stream);
 /* The same step from HOST arrays (pinned memory for asynchrony): pix_host and
@@ -271,9 +278,9 @@ nh_status launch_info(int32_t* out, int32_t n);
 /* ------------------------------------------------------------------ stage probes
  * The individual stages of the fused kernels, exposed for bitwise tests.
  * sample_rays: positions float[3 * n_rays * n_samples] ([ray][sample][xyz]) and
- * delta float[n_rays] of the ray sampler. */
+ * delta float[n_rays] of the ray sampler (jitter_seed as in nh_ray_batch). */
 nh_status sample_rays(const nh_geometry* g, int32_t view, int32_t n_rays, const int32_t* pix_dev,
-                      int32_t n_samples, float* xyz_dev, float* delta_dev, void* stream);
+                      int32_t n_samples, uint64_t jitter_seed, float* xyz_dev, float* delta_dev, void* stream);
 /* hash_corners: for n points, corner indices uint32[n][L][8] and weights float[n][L][8]. */
 nh_status hash_corners(const nh_field* f, int32_t n, const float* xyz_dev, uint32_t* idx_dev,
                        float* w_dev, void* stream);

@@ -22,7 +22,7 @@ transfer *gain* of Mapping Consistency Initialization, which has no closed form
 channel mask (mask.py) is pinned on pure tones, white noise and planted fields;
 the paper gives no grid, statistic or threshold, so those are a stated reading.
 """
-from .geometry import view_table, ray_setup, sample_points, voxel_centres_f32
+from .geometry import view_table, ray_setup, sample_points, voxel_centres_f32, splitmix64, stratum_offsets
 from .encoding import level_resolutions, corners, encode, encode_backward
 from .field import (unflatten, flatten, normalize_forward, normalize_backward,
                     mlp_forward, mlp_backward, field_forward, field_backward)
@@ -32,7 +32,7 @@ from .project import project
 from .mask import radial_frequency, high_frequency_fraction, mask_from_fraction, channel_mask
 
 __all__ = [
-    "view_table", "ray_setup", "sample_points", "voxel_centres_f32",
+    "view_table", "ray_setup", "sample_points", "voxel_centres_f32", "splitmix64", "stratum_offsets",
     "level_resolutions", "corners", "encode", "encode_backward",
     "unflatten", "flatten", "normalize_forward", "normalize_backward",
     "mlp_forward", "mlp_backward", "field_forward", "field_backward",

@@ -99,11 +99,39 @@ def ray_setup(tab, du, dv, nu, nv, view, pix):
     return o, dn, near, far, hit
 
 
-def sample_points(o, d, near, far, N):
-    """Midpoint samples x_i = o + t_i d (float32, (R, N, 3)) and Delta (R,)."""
+def splitmix64(seed, k):
+    """Output number k (k >= 1, uint64 array) of the SplitMix64 generator started at
+    `seed` (Steele, Lea and Flood, "Fast splittable pseudorandom number generators",
+    2014): the state advances by the golden-ratio increment and is then mixed."""
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) + np.uint64(0x9E3779B97F4A7C15) * np.asarray(k, dtype=np.uint64)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def stratum_offsets(seed, pix, N):
+    """Offsets u (R, N) float32 of each sample inside its stratum: 1/2 when seed is 0
+    (midpoint rule), else the top 24 bits of SplitMix64 output pix_r * N + i + 1
+    times 2^-24 (stratified jitter; exact in float32)."""
+    pix = np.asarray(pix)
+    if seed == 0:
+        return np.full((len(pix), N), f32(0.5), dtype=np.float32)
+    k = (pix.astype(np.uint64)[:, None] * np.uint64(N) + np.arange(N, dtype=np.uint64)[None, :]
+         + np.uint64(1))
+    return (splitmix64(seed, k) >> np.uint64(40)).astype(np.float32) * f32(2.0 ** -24)
+
+
+def sample_points(o, d, near, far, N, u=None):
+    """Samples x_i = o + t_i d (float32, (R, N, 3)) and Delta (R,), with
+    t_i = near + (i + u_i) Delta: the midpoint rule (u = 1/2) unless per-sample
+    stratum offsets u (R, N) are given."""
     delta = (far - near) / f32(N)
-    ti = np.arange(N, dtype=np.float32) + f32(0.5)
-    t = near[:, None] + ti[None, :] * delta[:, None]
+    if u is None:
+        ti = (np.arange(N, dtype=np.float32) + f32(0.5))[None, :]
+    else:
+        ti = np.arange(N, dtype=np.float32)[None, :] + np.asarray(u, dtype=np.float32)
+    t = near[:, None] + ti * delta[:, None]
     x = o[:, None, :] + t[:, :, None] * d[:, None, :]
     return x.astype(np.float32), delta.astype(np.float32)
 

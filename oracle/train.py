@@ -20,7 +20,7 @@ import dataclasses
 
 import numpy as np
 
-from .geometry import ray_setup, sample_points, voxel_centres_f32
+from .geometry import ray_setup, sample_points, stratum_offsets, voxel_centres_f32
 from .field import unflatten, flatten, field_forward, field_backward
 
 
@@ -35,12 +35,14 @@ class AdamState:
         return cls(np.zeros(n), np.zeros(n), 0)
 
 
-def render_forward(flat, cfg, geom, view, pix, N, mask=None):
-    """Predicted projections A (R,) of rays (view, pix). geom = (tab, du, dv, nu, nv)."""
+def render_forward(flat, cfg, geom, view, pix, N, mask=None, jitter_seed=0):
+    """Predicted projections A (R,) of rays (view, pix). geom = (tab, du, dv, nu, nv).
+    jitter_seed 0: midpoint samples; otherwise stratified jitter (stratum_offsets)."""
     tab, du, dv, nu, nv = geom
     p = unflatten(flat, cfg)
     o, d, near, far, hit = ray_setup(tab, du, dv, nu, nv, view, pix)
-    x, delta = sample_points(o, d, near, far, N)
+    u = stratum_offsets(jitter_seed, pix, N) if jitter_seed else None
+    x, delta = sample_points(o, d, near, far, N, u)
     R = len(pix)
     A = np.zeros(R)
     xh = x[hit].reshape(-1, 3)
@@ -51,9 +53,9 @@ def render_forward(flat, cfg, geom, view, pix, N, mask=None):
     return A, (p, cache, hit, delta, N)
 
 
-def render(flat, cfg, geom, view, pix, N, mask=None):
+def render(flat, cfg, geom, view, pix, N, mask=None, jitter_seed=0):
     """Eq. 1 for each ray of the batch."""
-    return render_forward(flat, cfg, geom, view, pix, N, mask)[0]
+    return render_forward(flat, cfg, geom, view, pix, N, mask, jitter_seed)[0]
 
 
 def loss_and_grad(A, A_meas, kind):
@@ -91,9 +93,9 @@ def adam_step(flat, grad, state, cfg, loss_scale=1.0):
     return new, AdamState(m, v, t), False
 
 
-def train_step(flat, state, cfg, geom, view, pix, A_meas, N, mask=None):
+def train_step(flat, state, cfg, geom, view, pix, A_meas, N, mask=None, jitter_seed=0):
     """One reconstruction step (Sec. 2.5): render, loss, backward, Adam."""
-    A, cache = render_forward(flat, cfg, geom, view, pix, N, mask)
+    A, cache = render_forward(flat, cfg, geom, view, pix, N, mask, jitter_seed)
     loss, dLdA = loss_and_grad(A, A_meas, cfg.loss)
     grad = render_backward(cache, dLdA, cfg)
     new, state, _ = adam_step(flat, grad, state, cfg)

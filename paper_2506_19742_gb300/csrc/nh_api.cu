@@ -60,7 +60,7 @@ extern "C" nh_status nh_last_error(char* buf, size_t n) {
     return NH_OK;
 }
 
-extern "C" int32_t nh_version(void) { return 100; }
+extern "C" int32_t nh_version(void) { return 101; }
 
 // ----------------------------------------------------------------------------- geometry
 struct nh_geometry {
@@ -112,8 +112,9 @@ extern "C" nh_status geometry_view_table(const nh_geometry* g, float* out, size_
     return NH_OK;
 }
 
-static ViewArgs view_args(const nh_geometry* g, int view) {
+static ViewArgs view_args(const nh_geometry* g, int view, uint64_t jitter = 0) {
     ViewArgs va;
+    va.jitter = jitter;
     const float* r = &g->tab[(size_t)view * 12];
     for (int k = 0; k < 3; k++) {
         va.s[k] = r[k];
@@ -424,8 +425,9 @@ static nh_status check_batch(const nh_field* f, const nh_geometry* g, const nh_r
 
 // Forward, loss and backward of one batch, accumulating into grads (R > 0).
 static nh_status run_accumulate(nh_field* f, const nh_geometry* g, int view, int R, const int32_t* pix,
-                                const float* a_meas, int N, float* loss_dev, const RayWs& w, cudaStream_t st) {
-    const ViewArgs va = view_args(g, view);
+                                const float* a_meas, int N, uint64_t jitter, float* loss_dev, const RayWs& w,
+                                cudaStream_t st) {
+    const ViewArgs va = view_args(g, view, jitter);
     const int C = (N + 31) / 32;
     if (C <= kMaxFusedChunks) {   // whole rays fit a CTA: one fused forward + loss + backward kernel
         NH_CUDA(launch_ray_train(f->fa, va, pix, a_meas, R, N, f->desc.loss, w.loss_part, loss_dev, st),
@@ -440,12 +442,13 @@ static nh_status run_accumulate(nh_field* f, const nh_geometry* g, int view, int
 }
 
 static nh_status run_train(nh_field* f, const nh_geometry* g, int view, int R, const int32_t* pix,
-                           const float* a_meas, int N, float* loss_dev, const RayWs& w, cudaStream_t st) {
+                           const float* a_meas, int N, uint64_t jitter, float* loss_dev, const RayWs& w,
+                           cudaStream_t st) {
     if (R == 0) {   // empty batch: loss 0, no update
         if (loss_dev) NH_CUDA(cudaMemsetAsync(loss_dev, 0, sizeof(float), st), "train_step");
         return NH_OK;
     }
-    const nh_status s = run_accumulate(f, g, view, R, pix, a_meas, N, loss_dev, w, st);
+    const nh_status s = run_accumulate(f, g, view, R, pix, a_meas, N, jitter, loss_dev, w, st);
     if (s != NH_OK) return s;
     NH_CUDA(launch_adam(f->fa, f->buf.params, f->buf.grads, f->buf.adam_m, f->buf.adam_v,
                         (int64_t)align_up(f->sizes.n_params, 4), f->desc.lr, f->desc.beta1, f->desc.beta2,
@@ -462,7 +465,8 @@ extern "C" nh_status accumulate_step(nh_field* f, const nh_geometry* g, const nh
         return NH_OK;
     }
     const RayWs w = ray_ws(ws, b->n_rays, b->n_samples);
-    return run_accumulate(f, g, b->view, b->n_rays, b->pix, b->a_meas, b->n_samples, loss_dev, w, S(stream));
+    return run_accumulate(f, g, b->view, b->n_rays, b->pix, b->a_meas, b->n_samples, b->jitter_seed, loss_dev, w,
+                          S(stream));
 }
 
 extern "C" nh_status train_step(nh_field* f, const nh_geometry* g, const nh_ray_batch* b, float* loss_dev,
@@ -470,7 +474,8 @@ extern "C" nh_status train_step(nh_field* f, const nh_geometry* g, const nh_ray_
     nh_status s = check_batch(f, g, b, ws, ws_bytes, true, "train_step");
     if (s != NH_OK) return s;
     const RayWs w = ray_ws(ws, b->n_rays, b->n_samples);
-    return run_train(f, g, b->view, b->n_rays, b->pix, b->a_meas, b->n_samples, loss_dev, w, S(stream));
+    return run_train(f, g, b->view, b->n_rays, b->pix, b->a_meas, b->n_samples, b->jitter_seed, loss_dev, w,
+                     S(stream));
 }
 
 extern "C" nh_status train_step_host(nh_field* f, const nh_geometry* g, int32_t view, int32_t R,
@@ -486,7 +491,7 @@ extern "C" nh_status train_step_host(nh_field* f, const nh_geometry* g, int32_t 
         NH_CUDA(cudaMemcpyAsync(w.pix, pix_host, sizeof(int32_t) * R, cudaMemcpyHostToDevice, st), "train_step_host pix");
         NH_CUDA(cudaMemcpyAsync(w.a_meas, a_meas_host, sizeof(float) * R, cudaMemcpyHostToDevice, st), "train_step_host a_meas");
     }
-    s = run_train(f, g, view, R, w.pix, w.a_meas, N, w.loss, w, st);
+    s = run_train(f, g, view, R, w.pix, w.a_meas, N, 0, w.loss, w, st);
     if (s != NH_OK) return s;
     NH_CUDA(cudaMemcpyAsync(loss_host, w.loss, sizeof(float), cudaMemcpyDeviceToHost, st), "train_step_host loss");
     return NH_OK;
@@ -499,7 +504,7 @@ extern "C" nh_status render_forward(const nh_field* f, const nh_geometry* g, con
     if (b->n_rays == 0) return NH_OK;
     if (!a_pred) return fail(NH_ERR_INVALID_ARG, "render_forward: null a_pred");
     const RayWs w = ray_ws(ws, b->n_rays, b->n_samples);
-    const ViewArgs va = view_args(g, b->view);
+    const ViewArgs va = view_args(g, b->view, b->jitter_seed);
     const int C = (b->n_samples + 31) / 32;
     NH_CUDA(launch_ray_forward(f->fa, va, b->pix, b->n_rays, b->n_samples, w.ray_part, S(stream)), "render_forward");
     NH_CUDA(launch_ray_loss(w.ray_part, b->n_rays, C, nullptr, f->desc.loss, a_pred, nullptr, nullptr, f->fa.state,
@@ -513,7 +518,7 @@ extern "C" nh_status render_backward(nh_field* f, const nh_geometry* g, const nh
     if (s != NH_OK) return s;
     if (b->n_rays == 0) return NH_OK;
     if (!dLdA) return fail(NH_ERR_INVALID_ARG, "render_backward: null dLdA");
-    const ViewArgs va = view_args(g, b->view);
+    const ViewArgs va = view_args(g, b->view, b->jitter_seed);
     NH_CUDA(launch_ray_backward(f->fa, va, b->pix, b->n_rays, b->n_samples, dLdA, S(stream)), "render_backward");
     return NH_OK;
 }
@@ -587,10 +592,10 @@ extern "C" nh_status project(const nh_geometry* g, const float* vol, int32_t D, 
 }
 
 extern "C" nh_status sample_rays(const nh_geometry* g, int32_t view, int32_t R, const int32_t* pix, int32_t N,
-                                 float* xyz, float* delta, void* stream) {
+                                 uint64_t jitter_seed, float* xyz, float* delta, void* stream) {
     if (!g || (R > 0 && (!pix || !xyz || !delta))) return fail(NH_ERR_INVALID_ARG, "sample_rays: null argument");
     if (view < 0 || view >= g->desc.n_views || R < 0 || N < 1) return fail(NH_ERR_INVALID_ARG, "sample_rays: bad sizes");
-    NH_CUDA(launch_sample_rays(view_args(g, view), pix, R, N, xyz, delta, S(stream)), "sample_rays");
+    NH_CUDA(launch_sample_rays(view_args(g, view, jitter_seed), pix, R, N, xyz, delta, S(stream)), "sample_rays");
     return NH_OK;
 }
 

@@ -67,9 +67,24 @@ __device__ __forceinline__ RayGeo ray_setup(const ViewArgs& V, int pix, int N) {
     return g;
 }
 
-// x_i = o + (near + (i + 1/2) delta) d
-__device__ __forceinline__ void sample_position(const RayGeo& g, int i, float x[3]) {
-    const float t = __fadd_rn(g.near, __fmul_rn(__fadd_rn((float)i, 0.5f), g.delta));
+// Offset u of sample i inside its stratum [i, i + 1) of the ray of pixel `pix`: 1/2
+// (the midpoint rule) when seed is 0, else stratified jitter: the top 24 bits of
+// output number pix * N + i + 1 of the SplitMix64 generator started at `seed`
+// (Steele, Lea and Flood, 2014), times 2^-24, exact in float32.
+__device__ __forceinline__ float stratum_offset(unsigned long long seed, int32_t pix, int N, int i) {
+    if (seed == 0ull) return 0.5f;
+    unsigned long long z = seed + 0x9E3779B97F4A7C15ull *
+                                      ((unsigned long long)(uint32_t)pix * (unsigned long long)N +
+                                       (unsigned long long)i + 1ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (float)(uint32_t)(z >> 40) * 0x1p-24f;
+}
+
+// x_i = o + (near + (i + u) delta) d
+__device__ __forceinline__ void sample_position(const RayGeo& g, int i, float u, float x[3]) {
+    const float t = __fadd_rn(g.near, __fmul_rn(__fadd_rn((float)i, u), g.delta));
 #pragma unroll
     for (int k = 0; k < 3; k++) x[k] = __fadd_rn(g.o[k], __fmul_rn(t, g.d[k]));
 }

@@ -199,7 +199,10 @@ __global__ void __launch_bounds__(256) k_ray_forward(FieldArgs fa, ViewArgs va,
     float mu = 0.f;
     if (kMmaPath<TT> || i < N) {
         float x[3];
-        sample_position(g, i < N ? i : N - 1, x);
+        {
+            const int ic = i < N ? i : N - 1;
+            sample_position(g, ic, stratum_offset(va.jitter, pix[r], N, ic), x);
+        }
         mu = point_mu<D, TT>(fa, cta, x, lane);
         if (i >= N) mu = 0.f;
     }
@@ -676,7 +679,8 @@ k_ray_backward(FieldArgs fa, ViewArgs va, const int32_t* __restrict__ pix, int R
         const int i = c * 32 + lane;
         const bool active = i < N;
         float x[3];
-        sample_position(g, active ? i : N - 1, x);
+        const int ic = active ? i : N - 1;
+        sample_position(g, ic, stratum_offset(va.jitter, pix[r], N, ic), x);
         const float gr = dLdA[r] * g.delta * scale;
         train_sample<D, G, TT>(fa, cta, x, active, lane, [gr](float) { return gr; });
     }
@@ -739,7 +743,8 @@ k_ray_train(FieldArgs fa, ViewArgs va, const int32_t* __restrict__ pix, const fl
         typename TrainCarry<D, G, TT>::type st;
         st.mu = 0.f;
         if (work) {
-            sample_position(g, i < N ? i : N - 1, x);
+            const int ic = i < N ? i : N - 1;
+            sample_position(g, ic, stratum_offset(va.jitter, pix[r], N, ic), x);
             if constexpr (kMmaPath<TT>)
                 mma_forward<D, G, TT>(fa, cta.sp, cta.sw, cta.smask, cta.wbuf, cta.tslot0, x, lane, st);
             else
@@ -877,7 +882,7 @@ static __global__ void k_sample_rays(ViewArgs va, const int32_t* __restrict__ pi
     const int r = (int)(t / N), i = (int)(t - (long long)r * N);
     const RayGeo g = ray_setup(va, pix[r], N);
     float x[3];
-    sample_position(g, i, x);
+    sample_position(g, i, stratum_offset(va.jitter, pix[r], N, i), x);
     xyz[3 * t] = x[0];
     xyz[3 * t + 1] = x[1];
     xyz[3 * t + 2] = x[2];

@@ -33,6 +33,7 @@ struct ViewArgs {
     float s[3], c[3], u[3], v[3];
     float du, dv;
     int32_t nu, nv;
+    unsigned long long jitter;   // 0: midpoint samples; else the stratified-jitter seed
 };
 
 // Everything a field kernel needs, passed by value.

@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(256) k_project(ViewArgs va, const float* __res
         float acc = 0.f;
         for (int i = 0; i < n; i++) {
             float x[3];
-            sample_position(g, i, x);
+            sample_position(g, i, 0.5f, x);
             int i0[3];
             float f[3];
 #pragma unroll

@@ -61,7 +61,7 @@ class FieldBuffers(C.Structure):
 
 class RayBatch(C.Structure):
     _fields_ = [("view", C.c_int32), ("n_rays", C.c_int32), ("pix", C.c_void_p),
-                ("a_meas", C.c_void_p), ("n_samples", C.c_int32)]
+                ("a_meas", C.c_void_p), ("n_samples", C.c_int32), ("jitter_seed", C.c_uint64)]
 
 
 _P = C.c_void_p
@@ -101,7 +101,7 @@ _SIGS = {
     "project": (_I, [_P, _P, _I, _I, _P, _P]),
     "volume_mse": (_I, [_P, _P, C.c_int64, _P, _P, _SZ, _P]),
     "launch_info": (_I, [C.POINTER(_I), _I]),
-    "sample_rays": (_I, [_P, _I, _I, _P, _I, _P, _P, _P]),
+    "sample_rays": (_I, [_P, _I, _I, _P, _I, C.c_uint64, _P, _P, _P]),
     "hash_corners": (_I, [_P, _I, _P, _P, _P, _P]),
     "encode_points": (_I, [_P, _I, _P, _P, _P]),
     "scatter_points": (_I, [_P, _I, _P, _P, _P]),
@@ -300,24 +300,25 @@ def workspace(nbytes: int, device="cuda"):
     return torch.empty(max(1, (nbytes + 3) // 4), dtype=torch.float32, device=device)
 
 
-def _batch(view, pix, a_meas, n_samples):
+def _batch(view, pix, a_meas, n_samples, jitter_seed=0):
+    """jitter_seed 0: midpoint samples; otherwise stratified jitter drawn from it."""
     pix = _dev(pix, torch.int32, "pix")
     a_meas = _dev(a_meas, torch.float32, "a_meas")
     n = 0 if pix is None else pix.numel()
     return RayBatch(int(view), n, pix.data_ptr() if pix is not None else None,
-                    a_meas.data_ptr() if a_meas is not None else None, int(n_samples))
+                    a_meas.data_ptr() if a_meas is not None else None, int(n_samples), int(jitter_seed))
 
 
 # ---------------------------------------------------------------------------- entry points
-def train_step(field, geom, view, pix, a_meas, n_samples, loss_out, ws, stream=None):
-    b = _batch(view, pix, a_meas, n_samples)
+def train_step(field, geom, view, pix, a_meas, n_samples, loss_out, ws, stream=None, jitter_seed=0):
+    b = _batch(view, pix, a_meas, n_samples, jitter_seed)
     _check(load().train_step(field.handle, geom.handle, C.byref(b), _ptr(loss_out), _ptr(ws),
                              ws.numel() * 4, _stream(stream)), "train_step")
 
 
-def accumulate_step(field, geom, view, pix, a_meas, n_samples, loss_out, ws, stream=None):
+def accumulate_step(field, geom, view, pix, a_meas, n_samples, loss_out, ws, stream=None, jitter_seed=0):
     """Forward + loss + backward into the field's gradients, no optimizer step."""
-    b = _batch(view, pix, a_meas, n_samples)
+    b = _batch(view, pix, a_meas, n_samples, jitter_seed)
     _check(load().accumulate_step(field.handle, geom.handle, C.byref(b), _ptr(loss_out), _ptr(ws),
                                   ws.numel() * 4, _stream(stream)), "accumulate_step")
 
@@ -332,23 +333,23 @@ def train_step_host(field, geom, view, pix_host, a_meas_host, n_samples, loss_ho
                                   ws.numel() * 4, _stream(stream)), "train_step_host")
 
 
-def render_forward(field, geom, view, pix, n_samples, a_pred, ws, stream=None):
-    b = _batch(view, pix, None, n_samples)
+def render_forward(field, geom, view, pix, n_samples, a_pred, ws, stream=None, jitter_seed=0):
+    b = _batch(view, pix, None, n_samples, jitter_seed)
     _check(load().render_forward(field.handle, geom.handle, C.byref(b), _ptr(a_pred), _ptr(ws),
                                  ws.numel() * 4, _stream(stream)), "render_forward")
 
 
-def render_forward_noalloc(field, geom, view, pix, n_samples, a_pred, stream=None):
+def render_forward_noalloc(field, geom, view, pix, n_samples, a_pred, stream=None, jitter_seed=0):
     """render_forward without a workspace argument, for callers that cannot allocate
     device memory at call time; its scratch is a fixed 1 MiB block inside the library
     (see include/nhcbct.h for the size limit and the rules on concurrent calls)."""
-    b = _batch(view, pix, None, n_samples)
+    b = _batch(view, pix, None, n_samples, jitter_seed)
     _check(load().render_forward_noalloc(field.handle, geom.handle, C.byref(b), _ptr(a_pred), _stream(stream)),
            "render_forward_noalloc")
 
 
-def render_backward(field, geom, view, pix, n_samples, dLdA, ws, stream=None):
-    b = _batch(view, pix, None, n_samples)
+def render_backward(field, geom, view, pix, n_samples, dLdA, ws, stream=None, jitter_seed=0):
+    b = _batch(view, pix, None, n_samples, jitter_seed)
     _check(load().render_backward(field.handle, geom.handle, C.byref(b), _ptr(dLdA), _ptr(ws),
                                   ws.numel() * 4, _stream(stream)), "render_backward")
 
@@ -419,10 +420,10 @@ def psnr(vol_pred, vol_gt, data_range=1.0, stream=None):
     return float("inf") if mse == 0 else 10.0 * math.log10(data_range * data_range / mse)
 
 
-def sample_rays(geom, view, pix, n_samples, xyz_out, delta_out, stream=None):
+def sample_rays(geom, view, pix, n_samples, xyz_out, delta_out, stream=None, jitter_seed=0):
     pix = _dev(pix, torch.int32, "pix")
-    _check(load().sample_rays(geom.handle, int(view), pix.numel(), _ptr(pix), int(n_samples), _ptr(xyz_out),
-                              _ptr(delta_out), _stream(stream)), "sample_rays")
+    _check(load().sample_rays(geom.handle, int(view), pix.numel(), _ptr(pix), int(n_samples), int(jitter_seed),
+                              _ptr(xyz_out), _ptr(delta_out), _stream(stream)), "sample_rays")
 
 
 def hash_corners(field, xyz, idx_out, w_out, stream=None):

@@ -38,10 +38,11 @@ class Reconstruction:
             self._ws_key = (R, N)
         return self._ws
 
-    def step(self, view, pix, a_meas, n_samples):
-        """One training step on device-resident pix (int32) / a_meas (float32)."""
+    def step(self, view, pix, a_meas, n_samples, jitter_seed=0):
+        """One training step on device-resident pix (int32) / a_meas (float32);
+        jitter_seed 0 samples at stratum midpoints, any other value jitters them."""
         nh.train_step(self.field, self.geom, view, pix, a_meas, n_samples, self.loss,
-                      self._workspace(pix.numel(), n_samples))
+                      self._workspace(pix.numel(), n_samples), jitter_seed=jitter_seed)
         self.steps += 1
 
     def volume(self, D):

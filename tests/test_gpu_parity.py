@@ -59,8 +59,9 @@ def _grad_close(g_gpu, g_orc, cfg, rtol=1e-3, what="", norm_rtol=None):
 
 
 # ------------------------------------------------------------------------------ stages
+@pytest.mark.parametrize("jitter", [0, 0x5EED0123456789AB])
 @pytest.mark.parametrize("N", [1, 37, 64, 200])
-def test_sampler_positions_and_deltas_are_bitwise(lib, N):
+def test_sampler_positions_and_deltas_are_bitwise(lib, N, jitter):
     geom = lib.Geometry.from_config(GEOM)
     tab, du, dv = geom.view_table()
     otab, odu, odv, nu, nv = oracle_geom(GEOM)
@@ -70,9 +71,10 @@ def test_sampler_positions_and_deltas_are_bitwise(lib, N):
     for view in (0, 2, 5):
         xyz = torch.empty(len(pix) * N * 3, device="cuda")
         delta = torch.empty(len(pix), device="cuda")
-        lib.sample_rays(geom, view, _t(pix), N, xyz, delta)
+        lib.sample_rays(geom, view, _t(pix), N, xyz, delta, jitter_seed=jitter)
         o, d, near, far, hit = oracle.ray_setup(otab, odu, odv, nu, nv, view, pix)
-        x, dl = oracle.sample_points(o, d, near, far, N)
+        u = oracle.stratum_offsets(jitter, pix, N) if jitter else None
+        x, dl = oracle.sample_points(o, d, near, far, N, u)
         g = _np(xyz).reshape(len(pix), N, 3)
         assert np.array_equal(_np(delta).view(np.uint32), dl.view(np.uint32))
         assert np.array_equal(g[hit].view(np.uint32), x[hit].view(np.uint32))
@@ -238,6 +240,32 @@ def test_train_step_fused_and_split_paths_match_oracle(lib, precision, N):
     expect = -cfg.lr * g / (np.abs(g) + cfg.adam_eps)
     agree = np.mean(np.abs(step[big] - expect[big]) < 0.1 * cfg.lr)
     assert agree > (0.999 if precision == S.PREC_F32 else 0.97), agree
+
+
+@pytest.mark.parametrize("N", [192, 520])
+def test_stratified_jitter_training_matches_oracle(lib, N):
+    """Stratified jitter (a new SplitMix64 seed per step): the fused (N = 192) and the
+    split (N = 520) paths give the oracle's loss for the same jittered samples, and
+    render_backward the oracle's gradient."""
+    cfg = field_cfg(n_levels=16, hidden_layers=4, log2_T=12, max_res=256)
+    flat = S.init_params(cfg, 41, table_scale=0.5).astype(np.float32)
+    field = lib.Field(cfg, params=flat)
+    geom = lib.Geometry.from_config(GEOM)
+    og = oracle_geom(GEOM)
+    pix = batch(GEOM, 4, 150, seed=N, n_miss=2)
+    a_meas = np.random.default_rng(N + 1).uniform(0, 0.8, size=len(pix)).astype(np.float32)
+    seed = 0xC0FFEE + N
+    A, cache = oracle.render_forward(flat.astype(np.float64), cfg, og, 4, pix, N, jitter_seed=seed)
+    A_mid = oracle.render(flat.astype(np.float64), cfg, og, 4, pix, N)
+    assert np.abs(A - A_mid).max() > 1e-6            # the jitter moves the samples
+    ref_loss, dLdA = oracle.loss_and_grad(A, a_meas, S.LOSS_MSE)
+    ws = lib.workspace(lib.step_workspace_bytes(field, len(pix), N))
+    lib.render_backward(field, geom, 4, _t(pix), N, _t(dLdA.astype(np.float32)), ws, jitter_seed=seed)
+    _grad_close(_np(field.flat_grads()), oracle.render_backward(cache, dLdA, cfg), cfg, what="jitter")
+    field.grads.zero_()
+    loss_t = torch.zeros(1, device="cuda")
+    lib.accumulate_step(field, geom, 4, _t(pix), _t(a_meas), N, loss_t, ws, jitter_seed=seed)
+    assert abs(_np(loss_t)[0] - ref_loss) <= 1e-5 * ref_loss
 
 
 def test_autograd_function_matches_oracle(lib):

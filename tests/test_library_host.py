@@ -35,7 +35,7 @@ def test_library_exports_every_declared_symbol(nh):
     for n in names:
         assert hasattr(lib, n), n
         assert n in nh.EXPORTS, n
-    assert lib.nh_version() == 100
+    assert lib.nh_version() == 101
     assert lib.nh_status_string(-3) == b"NH_ERR_SIZE_MISMATCH"
 
 

@@ -471,3 +471,31 @@ def test_channel_mask_keeps_a_smooth_dense_level_and_drops_a_hashed_noise_level(
     mask, frac = oracle.channel_mask(flat, cfg, G=32, cutoff=0.25, threshold=0.85)
     np.testing.assert_array_equal(mask, [1, 1, 0, 0])
     assert frac[:2].max() < 0.1 and frac[2:].min() > 0.85
+
+
+# ---------------------------------------------------------------- stratified jitter
+def test_splitmix64_reference_outputs_and_jittered_strata():
+    """SplitMix64 started at 1234567 gives the generator's published first outputs;
+    jittered samples stay inside their strata, are uniform there, and seed 0 is the
+    midpoint rule."""
+    out = oracle.splitmix64(1234567, np.arange(1, 6, dtype=np.uint64))
+    assert out.tolist() == [6457827717110365317, 3203168211198807973, 9817491932198370423,
+                            4593380528125082431, 16408922859458223821]
+    pix = np.arange(0, 4000, 7, dtype=np.int32)
+    u = oracle.stratum_offsets(99, pix, 64)
+    assert u.dtype == np.float32 and u.min() >= 0.0 and u.max() < 1.0
+    assert abs(u.mean() - 0.5) < 0.01 and abs(u.var() - 1 / 12) < 0.005
+    assert np.array_equal(u[3], oracle.stratum_offsets(99, pix[3:4], 64)[0])     # keyed by pixel
+    assert not np.array_equal(u, oracle.stratum_offsets(100, pix, 64))
+    assert np.all(oracle.stratum_offsets(0, pix, 64) == np.float32(0.5))
+    g = S.GeometryConfig(n_views=3, det_nu=16, det_nv=16)
+    tab, du, dv, nu, nv = _geom(g)
+    p16 = np.arange(nu * nv)
+    o, d, near, far, hit = oracle.ray_setup(tab, du, dv, nu, nv, 1, p16)
+    xm, delta = oracle.sample_points(o, d, near, far, 9)
+    xj, delta_j = oracle.sample_points(o, d, near, far, 9, oracle.stratum_offsets(5, p16, 9))
+    assert np.array_equal(delta, delta_j)
+    for r in np.nonzero(hit)[0]:
+        # distance of each jittered sample from the entry point, in units of Delta
+        s = np.linalg.norm(xj[r].astype(np.float64) - (o[r] + near[r] * d[r]).astype(np.float64), axis=1) / delta[r]
+        assert np.all(s > np.arange(9) - 1e-3) and np.all(s < np.arange(9) + 1 + 1e-3)
