@@ -58,7 +58,7 @@ def parse_args():
     p.add_argument("--no-psnr", action="store_true", help="skip the time-to-PSNR runs")
     p.add_argument("--no-l2", action="store_true", help="skip the gather / scatter L2 roofline probes")
     p.add_argument("--psnr-steps", type=int, default=3000, help="step cap of the time-to-PSNR runs")
-    p.add_argument("--experiment", default="", choices=["", "mci", "fftmask"])
+    p.add_argument("--experiment", default="", choices=["", "mci", "fftmask", "variants"])
     p.add_argument("--mask-step", type=int, default=500, help="fftmask: step at which the mask is chosen")
     p.add_argument("--mask-grid", type=int, default=64, help="fftmask: voxel grid of the feature spectra")
     p.add_argument("--mci-cases", type=int, default=8)
@@ -461,6 +461,70 @@ def l2_roofline(nh, torch, geom, fields, batch, N, dev):
     return out
 
 
+def train_arm(nh, torch, recon, cm, w, scan, seed, steps, jitter=False, mask_step=0, mask_grid=64):
+    """Trains workload w on a scan from seed's initialisation for `steps` steps; PSNR
+    every 50 steps (not timed). jitter: a new stratified-jitter seed every step;
+    mask_step > 0: FFT channel mask chosen at the end of the 50-step block holding
+    that step (between steps, outside the timed region)."""
+    geom, vol, a_meas_all, cands = scan
+    dev = torch.device("cuda", 0)
+    vol_gt = torch.from_numpy(vol.astype(np.float32).ravel()).to(dev)
+    rec = recon.Reconstruction(w.field, geom, params=S.init_params(w.field, seed))
+    it = device_batches(torch, w, cands, a_meas_all, 500, seed + 5, dev)
+    stream = torch.cuda.current_stream()
+    curve, reached, train_ms, out = [], {}, 0.0, {}
+    for s0 in range(0, steps, 50):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for s in range(s0 + 1, min(steps, s0 + 50) + 1):
+            view, pix, a = next(it)
+            rec.step(view, pix, a, w.n_samples, jitter_seed=(0x9E3779B9 * s + 1) if jitter else 0)
+        e1.record(stream)
+        e1.synchronize()
+        train_ms += e0.elapsed_time(e1)
+        if mask_step and s0 < mask_step <= s0 + 50:     # chosen between steps, not timed
+            mask, frac = cm.select_channel_mask(rec.field, G=mask_grid)
+            out["mask"] = mask.astype(int).tolist()
+            out["high_frequency_fraction"] = [round(float(x), 3) for x in frac]
+        p = rec.psnr(vol_gt)
+        curve.append((min(steps, s0 + 50), round(train_ms / 1e3, 4), round(p, 3)))
+        for t in (25.0, 30.0, 35.0):
+            if t not in reached and p >= t:
+                reached[t] = (curve[-1][0], curve[-1][1])
+    out.update({"final_psnr": curve[-1][2], "best_psnr": max(c[2] for c in curve),
+                "steps_to": {str(t): reached[t][0] if t in reached else None for t in (25.0, 30.0, 35.0)},
+                "seconds_to": {str(t): reached[t][1] if t in reached else None for t in (25.0, 30.0, 35.0)},
+                "ms_per_step": round(train_ms / steps, 4), "psnr_at": [c[::2] for c in curve[:: max(1, len(curve) // 12)]]})
+    return out
+
+
+def run_variants(args):
+    """The paper's own step shape and sampling (Sec. 3.1: one view, 1024 rays x 320
+    samples, the L1 loss of Eq. 3) against the benchmark's (2048 x 192, squared error,
+    midpoint samples), with stratified jitter and with FFT channel masking, on the same
+    scan and initialisation."""
+    import torch
+    from paper_2506_19742_gb300 import build as nhbuild
+    from paper_2506_19742_gb300 import channel_mask as cm
+    from paper_2506_19742_gb300 import nhcbct as nh
+    from paper_2506_19742_gb300 import recon
+    nhbuild.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    base = S.WORKLOADS[args.workload]
+    faithful = S.WORKLOADS["paper320_fp32" if base.field.precision == S.PREC_F32 else "paper320_bf16"]
+    scan = make_scan(nh, torch, base, args.seed, dev)
+    arms = [("bench shape: 2048 x 192, MSE, midpoint", base, {}),
+            ("paper shape: 1024 x 320, L1, midpoint", faithful, {}),
+            ("paper shape, stratified jitter", faithful, {"jitter": True}),
+            ("paper shape, jitter + FFT mask at step 500", faithful, {"jitter": True, "mask_step": 500})]
+    out = {"experiment": "variants", "steps": args.psnr_steps, "arms": {}}
+    for name, w, kw in arms:
+        out["arms"][name] = {"workload": w.name, **train_arm(nh, torch, recon, cm, w, scan, args.seed,
+                                                            args.psnr_steps, **kw)}
+    print(json.dumps(out))
+
+
 def run_fftmask(args):
     """FFT channel masking (Sec. 2.3) on the benchmark scan: the same initialisation
     and batches trained with no mask, and with the mask chosen from the hash
@@ -732,6 +796,9 @@ def main():
     elif args.experiment == "fftmask":
         if rank == 0:
             run_fftmask(args)
+    elif args.experiment == "variants":
+        if rank == 0:
+            run_variants(args)
     elif args.impl == "reference":
         run_reference(args, rank, world)
     else:
