@@ -252,12 +252,13 @@ static __global__ void __launch_bounds__(1024) k_ray_loss(const float* __restric
 }
 
 // ============================================================================ backward
-// Per-warp shared scratch (floats): stage [32][kW+1] (one layer input, a row per
-// sample, for the transposed weight-gradient reduction) and dz [32][kW]
-// (XOR-swizzled float4 groups). Each sample's activations live in TMEM: slot 0
-// holds hhat (or h without normalization), slot k (1 <= k < H) holds a_k, the
-// ReLU output of layer k-1; a_H stays in registers.
-constexpr int kStage = 32 * (kW + 1);
+// Per-warp shared scratch (floats) of the FFMA path: stage [32][kW] (one layer
+// input, a row per sample) and dz [32][kW], both with XOR-swizzled float4 groups
+// (element j of row s at swz(s, j)), so that row writes, column reads and float4
+// reads of any group are conflict-free. Each sample's activations live in TMEM:
+// slot 0 holds hhat (or h without normalization), slot k (1 <= k < H) holds a_k,
+// the ReLU output of layer k-1; a_H waits in the stage tile.
+constexpr int kStage = 32 * kW;
 __host__ __device__ constexpr int warp_scratch_floats() { return kStage + 32 * kW; }
 constexpr int kBwdWarps = 8;
 constexpr int kMaxTrainWarps = kMaxFusedChunks;
@@ -269,39 +270,76 @@ __device__ __forceinline__ int swz(int s, int j) {   // column j of dz row s
 template <int IN>
 __device__ __forceinline__ void stage_row(float* stage, int lane, const float (&v)[IN]) {
 #pragma unroll
-    for (int j = 0; j < IN; j++) stage[lane * (kW + 1) + j] = v[j];
+    for (int q = 0; q < IN / 4; q++)
+        *reinterpret_cast<float4*>(stage + swz(lane, 4 * q)) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2],
+                                                                           v[4 * q + 3]);
+}
+
+// Column permutation of the FFMA path's shared-memory accumulators of W_l: element
+// (j, i) lives at j IN + fswz(i, j, IN). A lane of warp_weight_grad owns a block of
+// JPL consecutive rows j and 4 consecutive columns i; the permutation puts the 32
+// lanes of each accumulation step on 32 banks (2-way for IN = 16).
+__host__ __device__ __forceinline__ int fswz(int i, int j, int IN) {
+    return IN == 32 ? (i ^ ((j >> 3) & 3)) : (i ^ ((j >> 2) & 3));
 }
 
 // Stores this lane's dz row, then the warp reduces dW[j][i] = sum_s dz[s][j] in[s][i]
-// (lane i; in[s][i] = ga_i * stage[s][i] + be_i) and db[j] = sum_s dz[s][j] (lane j)
-// into the CTA accumulators.
-template <int IN>
+// (in[s][i] = ga_i * stage[s][i] + be_i; ga = gamma m, be = beta m for layer 0 with
+// normalization, else 1, 0) and db[j] = sum_s dz[s][j] (lane j) into the CTA
+// accumulators. Register blocking: lane (jb, ib) keeps the JPL x 4 block
+// j in [jb JPL, jb JPL + JPL), i in [4 ib, 4 ib + 4), reading per sample one float4
+// of the stage row and JPL / 4 float4 of the dz row (broadcast within a block row).
+template <int IN, bool AFFINE>
 __device__ __forceinline__ void warp_weight_grad(float* dzb, const float* stage, const float (&dz)[kW],
-                                                 float ga, float be, float* sgW, float* sgb, int lane) {
+                                                 const float* gamma, const float* beta, const float* mask,
+                                                 float* sgW, float* sgb, int lane) {
+    constexpr int IB = IN / 4;        // column groups of 4
+    constexpr int JPL = IB;           // rows per lane (8 for IN = 32, 4 for IN = 16)
 #pragma unroll
     for (int q = 0; q < kW / 4; q++)
-        *reinterpret_cast<float4*>(dzb + lane * kW + (((q ^ (lane & 7))) << 2)) =
+        *reinterpret_cast<float4*>(dzb + swz(lane, 4 * q)) =
             make_float4(dz[4 * q], dz[4 * q + 1], dz[4 * q + 2], dz[4 * q + 3]);
     __syncwarp();
-    if (lane < IN) {
-        float acc[kW];
+    const int ib = lane % IB, jb = lane / IB;
+    float ga[4] = {1.f, 1.f, 1.f, 1.f}, be[4] = {0.f, 0.f, 0.f, 0.f};
+    if constexpr (AFFINE) {
 #pragma unroll
-        for (int j = 0; j < kW; j++) acc[j] = 0.f;
+        for (int t = 0; t < 4; t++) {
+            const int i = 4 * ib + t;
+            ga[t] = (gamma ? gamma[i] : 1.f) * mask[i];
+            be[t] = gamma ? beta[i] * mask[i] : 0.f;
+        }
+    }
+    float acc[JPL][4];
+#pragma unroll
+    for (int jj = 0; jj < JPL; jj++)
+#pragma unroll
+        for (int t = 0; t < 4; t++) acc[jj][t] = 0.f;
 #pragma unroll 2
-        for (int s = 0; s < 32; s++) {
-            const float a = fmaf(ga, stage[s * (kW + 1) + lane], be);
+    for (int s = 0; s < 32; s++) {
+        const float4 a4 = *reinterpret_cast<const float4*>(stage + swz(s, 4 * ib));
+        float a[4] = {a4.x, a4.y, a4.z, a4.w};
+        if constexpr (AFFINE) {
 #pragma unroll
-            for (int q = 0; q < kW / 4; q++) {
-                const float4 d = *reinterpret_cast<const float4*>(dzb + s * kW + ((q ^ (s & 7)) << 2));
-                acc[4 * q] = fmaf(d.x, a, acc[4 * q]);
-                acc[4 * q + 1] = fmaf(d.y, a, acc[4 * q + 1]);
-                acc[4 * q + 2] = fmaf(d.z, a, acc[4 * q + 2]);
-                acc[4 * q + 3] = fmaf(d.w, a, acc[4 * q + 3]);
-            }
+            for (int t = 0; t < 4; t++) a[t] = fmaf(ga[t], a[t], be[t]);
         }
 #pragma unroll
-        for (int j = 0; j < kW; j++) atomicAdd(sgW + j * IN + wswz(lane, j, IN), acc[j]);
+        for (int q = 0; q < JPL / 4; q++) {
+            const float4 d = *reinterpret_cast<const float4*>(dzb + swz(s, 4 * (jb * (JPL / 4) + q)));
+            const float dv[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+            for (int e = 0; e < 4; e++)
+#pragma unroll
+                for (int t = 0; t < 4; t++) acc[4 * q + e][t] = fmaf(dv[e], a[t], acc[4 * q + e][t]);
+        }
     }
+#pragma unroll
+    for (int jj = 0; jj < JPL; jj++)
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            const int j = jb * JPL + jj, i = 4 * ib + t;
+            atomicAdd(sgW + j * IN + fswz(i, j, IN), acc[jj][t]);
+        }
     float bsum = 0.f;
 #pragma unroll 8
     for (int s = 0; s < 32; s++) bsum += dzb[swz(s, lane)];
@@ -430,12 +468,18 @@ __device__ __forceinline__ void ffma_backward(const FieldArgs& fa, const float* 
     dzb[lane] = dzo;
     float dz[kW];
 #pragma unroll
-    for (int j = 0; j < kW; j++) dz[j] = (stage[lane * (kW + 1) + j] > 0.f) ? wo[j] * dzo : 0.f;
+    for (int q = 0; q < kW / 4; q++) {
+        const float4 a4 = *reinterpret_cast<const float4*>(stage + swz(lane, 4 * q));
+        dz[4 * q] = a4.x > 0.f ? wo[4 * q] * dzo : 0.f;
+        dz[4 * q + 1] = a4.y > 0.f ? wo[4 * q + 1] * dzo : 0.f;
+        dz[4 * q + 2] = a4.z > 0.f ? wo[4 * q + 2] * dzo : 0.f;
+        dz[4 * q + 3] = a4.w > 0.f ? wo[4 * q + 3] * dzo : 0.f;
+    }
     __syncwarp();
     {
         float acc = 0.f;
 #pragma unroll 8
-        for (int t = 0; t < 32; t++) acc = fmaf(dzb[t], stage[t * (kW + 1) + lane], acc);
+        for (int t = 0; t < 32; t++) acc = fmaf(dzb[t], stage[swz(t, lane)], acc);
         atomicAdd(sg + lay.W(H) + lane, acc);
         const float bs = warp_sum(dzo);
         if (lane == 0) atomicAdd(sg + lay.b(H), bs);
@@ -453,7 +497,7 @@ __device__ __forceinline__ void ffma_backward(const FieldArgs& fa, const float* 
             for (int i = 0; i < kW; i++) pos |= (ak[i] > 0.f ? 1u : 0u) << i;
             stage_row<kW>(stage, lane, ak);
         }
-        warp_weight_grad<kW>(dzb, stage, dz, 1.f, 0.f, sg + lay.W(k), sg + lay.b(k), lane);
+        warp_weight_grad<kW, false>(dzb, stage, dz, nullptr, nullptr, nullptr, sg + lay.W(k), sg + lay.b(k), lane);
         float din[kW];
         linear_bwd_data<kW, kW>(sp + lay.W(k), dz, din);
 #pragma unroll
@@ -465,12 +509,8 @@ __device__ __forceinline__ void ffma_backward(const FieldArgs& fa, const float* 
     tmem_ld(tslot0, hhat);
     stage_row<D>(stage, lane, hhat);
     const bool affine = fa.norm != NH_NORM_NONE;
-    {
-        const int il = lane < D ? lane : 0;
-        const float ga = (affine ? sp[il] : 1.f) * smask[il];
-        const float be = affine ? sp[D + il] * smask[il] : 0.f;
-        warp_weight_grad<D>(dzb, stage, dz, ga, be, sg + lay.W(0), sg + lay.b(0), lane);
-    }
+    warp_weight_grad<D, true>(dzb, stage, dz, affine ? sp : nullptr, affine ? sp + D : nullptr, smask,
+                              sg + lay.W(0), sg + lay.b(0), lane);
     float dh[D];
     linear_bwd_data<D, kW>(sp + lay.W(0), dz, dh);   // dh <- dL/dy
     nhe_backward_scatter<D, G>(fa, sp, smask, sg, dzb, hhat, s.rstd, dh, x, active, lane);
@@ -653,7 +693,7 @@ __device__ __forceinline__ void bwd_end(const FieldArgs& fa, const BwdCta& c, ui
             const int IN = l == 0 ? fa.D : kW, o = k - lay.W(l);
             if (o >= 0 && o < kW * IN) {
                 const int j = o / IN, i = o - j * IN;
-                p = lay.W(l) + j * IN + wswz(i, j, IN);
+                p = lay.W(l) + j * IN + (fa.precision == NH_PREC_F32 ? fswz(i, j, IN) : wswz(i, j, IN));
             }
         }
         const float v = c.sg[p];
