@@ -315,7 +315,7 @@ __device__ __forceinline__ void warp_weight_grad(float* dzb, const float* stage,
     for (int jj = 0; jj < JPL; jj++)
 #pragma unroll
         for (int t = 0; t < 4; t++) acc[jj][t] = 0.f;
-#pragma unroll 2
+#pragma unroll 1
     for (int s = 0; s < 32; s++) {
         const float4 a4 = *reinterpret_cast<const float4*>(stage + swz(s, 4 * ib));
         float a[4] = {a4.x, a4.y, a4.z, a4.w};
