@@ -58,7 +58,7 @@ def parse_args():
     p.add_argument("--no-psnr", action="store_true", help="skip the time-to-PSNR runs")
     p.add_argument("--no-l2", action="store_true", help="skip the gather / scatter L2 roofline probes")
     p.add_argument("--psnr-steps", type=int, default=3000, help="step cap of the time-to-PSNR runs")
-    p.add_argument("--experiment", default="", choices=["", "mci", "fftmask", "variants"])
+    p.add_argument("--experiment", default="", choices=["", "mci", "fftmask", "variants", "ablation"])
     p.add_argument("--mask-step", type=int, default=500, help="fftmask: step at which the mask is chosen")
     p.add_argument("--mask-grid", type=int, default=64, help="fftmask: voxel grid of the feature spectra")
     p.add_argument("--mci-cases", type=int, default=8)
@@ -461,7 +461,7 @@ def l2_roofline(nh, torch, geom, fields, batch, N, dev):
     return out
 
 
-def train_arm(nh, torch, recon, cm, w, scan, seed, steps, jitter=False, mask_step=0, mask_grid=64):
+def train_arm(nh, torch, recon, cm, w, scan, seed, steps, jitter=False, mask_step=0, mask_grid=64, ln_mlp=None):
     """Trains workload w on a scan from seed's initialisation for `steps` steps; PSNR
     every 50 steps (not timed). jitter: a new stratified-jitter seed every step;
     mask_step > 0: FFT channel mask chosen at the end of the 50-step block holding
@@ -470,6 +470,8 @@ def train_arm(nh, torch, recon, cm, w, scan, seed, steps, jitter=False, mask_ste
     dev = torch.device("cuda", 0)
     vol_gt = torch.from_numpy(vol.astype(np.float32).ravel()).to(dev)
     rec = recon.Reconstruction(w.field, geom, params=S.init_params(w.field, seed))
+    if ln_mlp is not None:
+        recon.transfer(ln_mlp, rec.field)
     it = device_batches(torch, w, cands, a_meas_all, 500, seed + 5, dev)
     stream = torch.cuda.current_stream()
     curve, reached, train_ms, out = [], {}, 0.0, {}
@@ -494,7 +496,8 @@ def train_arm(nh, torch, recon, cm, w, scan, seed, steps, jitter=False, mask_ste
     out.update({"final_psnr": curve[-1][2], "best_psnr": max(c[2] for c in curve),
                 "steps_to": {str(t): reached[t][0] if t in reached else None for t in (25.0, 30.0, 35.0)},
                 "seconds_to": {str(t): reached[t][1] if t in reached else None for t in (25.0, 30.0, 35.0)},
-                "ms_per_step": round(train_ms / steps, 4), "psnr_at": [c[::2] for c in curve[:: max(1, len(curve) // 12)]]})
+                "ms_per_step": round(train_ms / steps, 4), "psnr_at": [c[::2] for c in curve[:: max(1, len(curve) // 12)]],
+                "curve": [c[::2] for c in curve]})
     return out
 
 
@@ -520,8 +523,50 @@ def run_variants(args):
             ("paper shape, jitter + FFT mask at step 500", faithful, {"jitter": True, "mask_step": 500})]
     out = {"experiment": "variants", "steps": args.psnr_steps, "arms": {}}
     for name, w, kw in arms:
-        out["arms"][name] = {"workload": w.name, **train_arm(nh, torch, recon, cm, w, scan, args.seed,
-                                                            args.psnr_steps, **kw)}
+        r = train_arm(nh, torch, recon, cm, w, scan, args.seed, args.psnr_steps, **kw)
+        r.pop("curve")
+        out["arms"][name] = {"workload": w.name, **r}
+    print(json.dumps(out))
+
+
+def run_ablation(args):
+    """The paper's ablation grid (Sec. 3.4) on one held-out scan: hash-feature
+    normalization (LayerNorm or none, Sec. 2.3) x initialisation (random, or MCI
+    pre-trained with the same normalization, Sec. 2.4) x FFT channel mask (none, or
+    chosen at step --mask-step). MCI here pre-trains on --mci-cases reconstructions."""
+    import dataclasses
+    import torch
+    from paper_2506_19742_gb300 import build as nhbuild
+    from paper_2506_19742_gb300 import channel_mask as cm
+    from paper_2506_19742_gb300 import nhcbct as nh
+    from paper_2506_19742_gb300 import recon
+    nhbuild.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    base = S.WORKLOADS[args.workload]
+    out = {"experiment": "ablation", "workload": base.name, "steps": args.psnr_steps, "mci_cases": args.mci_cases,
+           "mci_recon_steps": args.mci_recon_steps, "mci_pretrain_steps": args.mci_pretrain_steps,
+           "mask_step": args.mask_step, "arms": {}}
+    scan = make_scan(nh, torch, base, 200 + args.seed, dev)
+    for norm_name, norm in (("LN", S.NORM_LN), ("none", S.NORM_NONE)):
+        w = dataclasses.replace(base, field=dataclasses.replace(base.field, norm=norm))
+        vols = []
+        for c in range(100, 100 + args.mci_cases):
+            _, rec = time_to_psnr(nh, torch, recon, w, c, dev, targets=(99.0,), max_steps=args.mci_recon_steps,
+                                  eval_every=args.mci_recon_steps)
+            vols.append(rec.volume(w.vol_D))
+            del rec
+        shared, _ = recon.pretrain_mci(w.field, vols, steps=args.mci_pretrain_steps, points_per_step=65536,
+                                       seed=args.seed)
+        del vols
+        for init in ("random", "MCI"):
+            for mask in (0, args.mask_step):
+                name = f"norm={norm_name} init={init} mask={'step %d' % mask if mask else 'none'}"
+                r = train_arm(nh, torch, recon, cm, w, scan, 200 + args.seed, args.psnr_steps, mask_step=mask,
+                              ln_mlp=shared if init == "MCI" else None)
+                out["arms"][name] = {k: r[k] for k in ("final_psnr", "best_psnr", "steps_to", "seconds_to")}
+                at = dict((c[0], c[1]) for c in r["curve"])
+                out["arms"][name]["psnr_at_step"] = {t: at.get(t) for t in (50, 100, 200, 500, 1000)}
     print(json.dumps(out))
 
 
@@ -799,6 +844,9 @@ def main():
     elif args.experiment == "variants":
         if rank == 0:
             run_variants(args)
+    elif args.experiment == "ablation":
+        if rank == 0:
+            run_ablation(args)
     elif args.impl == "reference":
         run_reference(args, rank, world)
     else:
