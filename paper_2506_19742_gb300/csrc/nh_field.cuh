@@ -421,20 +421,28 @@ __device__ __forceinline__ void ffma_forward(const FieldArgs& fa, const float* s
     constexpr int L = D / 2;
     const DenseLayout lay{D, fa.H};
     const int H = fa.H;
+    // With D = kW layer 0 runs in the hidden layers' loop: one copy of the unrolled
+    // layer code instead of two keeps more of the kernel in the instruction cache.
+    constexpr int k0 = (D == kW) ? 0 : 1;
     float a[kW];
     {
         float h[D], hhat[D], y[D];
         encode_point<L, TT>(fa, table_base<TT>(fa), x, h);
         nhe_forward<D, G>(fa, sp, smask, h, hhat, s.rstd, y);
         tmem_st(tslot0, hhat);
-        float z[kW];
-        linear_fwd<D, kW>(sp + lay.W(0), sp + lay.b(0), y, z);
+        if constexpr (D == kW) {
 #pragma unroll
-        for (int j = 0; j < kW; j++) a[j] = fmaxf(z[j], 0.f);
+            for (int j = 0; j < kW; j++) a[j] = y[j];
+        } else {
+            float z[kW];
+            linear_fwd<D, kW>(sp + lay.W(0), sp + lay.b(0), y, z);
+#pragma unroll
+            for (int j = 0; j < kW; j++) a[j] = fmaxf(z[j], 0.f);
+        }
     }
 #pragma unroll 1
-    for (int k = 1; k < H; k++) {
-        tmem_st(tslot0 + 32 * k, a);
+    for (int k = k0; k < H; k++) {
+        if (k > 0) tmem_st(tslot0 + 32 * k, a);
         float z[kW];
         linear_fwd<kW, kW>(sp + lay.W(k), sp + lay.b(k), a, z);
 #pragma unroll

@@ -636,3 +636,37 @@ def test_fft_channel_mask_matches_oracle(lib):
         assert np.array_equal(mask[clear], ref_mask[clear].astype(np.float32)), (frac, ref_frac)
         masks.append(mask)
     np.testing.assert_array_equal(masks[0], [1] * 14 + [0, 0])
+
+
+# ------------------------------------------------------------------------------ stored record
+def test_library_matches_the_stored_oracle_step(lib):
+    """The library against tests/golden/oracle_step.json (the oracle's record of one
+    seeded step): A and the loss within 1e-5, the recorded gradient entries within
+    1e-3 of the largest gradient, and, where the gradient is not tiny, the entries
+    after one Adam step."""
+    import json
+    import os
+    import sys
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    sys.path.insert(0, here)
+    import make_golden
+    ref = json.load(open(os.path.join(here, "oracle_step.json")))
+    _, flat, pix, a_meas = make_golden.case()
+    cfg, N, view = make_golden.FIELD, make_golden.N, make_golden.VIEW
+    assert pix.tolist() == ref["pix"]
+    field = lib.Field(cfg, params=flat.astype(np.float32))
+    geom = lib.Geometry.from_config(make_golden.GEOM)
+    ws = lib.workspace(lib.step_workspace_bytes(field, len(pix), N))
+    a = torch.empty(len(pix), device="cuda")
+    lib.render_forward(field, geom, view, _t(pix), N, a, ws)
+    np.testing.assert_allclose(_np(a), ref["A"], rtol=1e-5, atol=1e-7)
+    loss_t = torch.zeros(1, device="cuda")
+    lib.accumulate_step(field, geom, view, _t(pix), _t(a_meas), N, loss_t, ws)
+    assert abs(_np(loss_t)[0] - ref["loss"]) <= 1e-5 * ref["loss"]
+    g = _np(field.flat_grads())[ref["grad_index"]]
+    assert np.abs(g - np.array(ref["grad_value"])).max() <= 1e-3 * ref["grad_max"]
+    lib.optimizer_step(field)
+    p = _np(field.flat_params())[ref["grad_index"]]
+    big = np.abs(np.array(ref["grad_value"])) > 1e-2 * ref["grad_max"]   # step sign not decided by rounding
+    assert big.sum() >= 8
+    np.testing.assert_allclose(p[big], np.array(ref["param_after_adam"])[big], rtol=0, atol=2e-6)

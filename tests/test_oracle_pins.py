@@ -499,3 +499,23 @@ def test_splitmix64_reference_outputs_and_jittered_strata():
         # distance of each jittered sample from the entry point, in units of Delta
         s = np.linalg.norm(xj[r].astype(np.float64) - (o[r] + near[r] * d[r]).astype(np.float64), axis=1) / delta[r]
         assert np.all(s > np.arange(9) - 1e-3) and np.all(s < np.arange(9) + 1 + 1e-3)
+
+
+# ---------------------------------------------------------------- stored record
+def test_oracle_reproduces_its_stored_step():
+    """tests/golden/oracle_step.json (written by tests/golden/make_golden.py from the
+    oracle alone) still matches the oracle: a change to the oracle's arithmetic shows
+    up here and must be justified and the record rewritten."""
+    import json
+    import os
+    import sys
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    sys.path.insert(0, here)
+    import make_golden
+    ref = json.load(open(os.path.join(here, "oracle_step.json")))
+    now = make_golden.expected()
+    assert now["pix"] == ref["pix"] and now["grad_index"] == ref["grad_index"]
+    np.testing.assert_allclose(now["A"], ref["A"], rtol=1e-12, atol=0)
+    assert abs(now["loss"] - ref["loss"]) <= 1e-12 * ref["loss"]
+    np.testing.assert_allclose(now["grad_value"], ref["grad_value"], rtol=1e-10, atol=1e-15)
+    np.testing.assert_allclose(now["param_after_adam"], ref["param_after_adam"], rtol=1e-12, atol=0)
