@@ -755,6 +755,18 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         if mixed is not None:
             flds[mixed["workload"]] = field_m
         l2 = l2_roofline(nh, torch, geom, flds, dev_batches[W], N, dev)
+        # the fused kernel against the time its gather and scatter take on their own
+        # (each at the L2's random-access limit): the share of the kernel that the
+        # table traffic alone would need
+        st = l2[w.name]
+        floor = st["gather"]["ms"] + st["scatter"]["ms"]
+        roofline["random_access_floor_ms"] = round(floor, 4)
+        roofline["frac_random_access_floor"] = round(floor / t_acc, 4)
+        if mixed is not None:
+            stm = l2[mixed["workload"]]
+            fm = stm["gather"]["ms"] + stm["scatter"]["ms"]
+            mixed["random_access_floor_ms"] = round(fm, 4)
+            mixed["frac_random_access_floor"] = round(fm / mixed["launch_ms"]["forward+loss+backward"], 4)
 
     # time to PSNR: FP32 and the mixed-precision workload on the same scan
     psnr = None
