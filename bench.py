@@ -58,7 +58,8 @@ def parse_args():
     p.add_argument("--no-psnr", action="store_true", help="skip the time-to-PSNR runs")
     p.add_argument("--no-l2", action="store_true", help="skip the gather / scatter L2 roofline probes")
     p.add_argument("--psnr-steps", type=int, default=3000, help="step cap of the time-to-PSNR runs")
-    p.add_argument("--experiment", default="", choices=["", "mci", "fftmask", "variants", "ablation"])
+    p.add_argument("--experiment", default="", choices=["", "mci", "fftmask", "variants", "ablation", "variation"])
+    p.add_argument("--variation-steps", type=int, default=1500, help="variation: training steps per arm")
     p.add_argument("--mask-step", type=int, default=500, help="fftmask: step at which the mask is chosen")
     p.add_argument("--mask-grid", type=int, default=64, help="fftmask: voxel grid of the feature spectra")
     p.add_argument("--mci-cases", type=int, default=8)
@@ -570,6 +571,54 @@ def run_ablation(args):
     print(json.dumps(out))
 
 
+def run_variation(args):
+    """The MLP-variation probe behind the paper's motivation for the Normalized Hash
+    Encoder (Sec. 1 and 2.3, Fig. 3): hash features come from a different subset of
+    table entries every step while every MLP weight moves, so the network's mapping
+    drifts. Every 100 steps the hash tables and mu at P fixed points are recorded;
+    100 steps later the recorded tables are evaluated with the current LN + MLP
+    (field_export / field_import of NH_PART_HASH and NH_PART_LN | NH_PART_MLP), and
+    the mean |mu_later(features_then) - mu_then| is the variation. Run with and
+    without the normalization on the same scan and initialisation."""
+    import dataclasses
+    import torch
+    from paper_2506_19742_gb300 import build as nhbuild
+    from paper_2506_19742_gb300 import nhcbct as nh
+    from paper_2506_19742_gb300 import recon
+    nhbuild.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    base = S.WORKLOADS[args.workload]
+    geom, vol, a_meas_all, cands = make_scan(nh, torch, base, args.seed, dev)
+    vol_gt = torch.from_numpy(vol.astype(np.float32).ravel()).to(dev)
+    xyz = torch.from_numpy(np.random.default_rng(args.seed + 9).random((65536, 3)).astype(np.float32)).to(dev)
+    out = {"experiment": "variation", "workload": base.name, "points": 65536, "interval": 100, "arms": {}}
+    for norm_name, norm in (("LN", S.NORM_LN), ("none", S.NORM_NONE)):
+        cfg = dataclasses.replace(base.field, norm=norm)
+        w = dataclasses.replace(base, field=cfg)
+        rec = recon.Reconstruction(cfg, geom, params=S.init_params(cfg, args.seed))
+        probe = nh.Field(cfg, params=S.init_params(cfg, args.seed))
+        it = device_batches(torch, w, cands, a_meas_all, 500, args.seed + 5, dev)
+        mu_then = torch.empty(65536, device=dev)
+        mu_now = torch.empty(65536, device=dev)
+        tables_then, series = None, []
+        for s in range(1, args.variation_steps + 1):
+            view, pix, a = next(it)
+            rec.step(view, pix, a, w.n_samples)
+            if s % 100 == 0:
+                if tables_then is not None:
+                    probe.import_(nh.PART_HASH, tables_then)
+                    probe.import_(nh.PART_LN | nh.PART_MLP, rec.field.export(nh.PART_LN | nh.PART_MLP))
+                    nh.query_points(probe, xyz, mu_now)
+                    series.append((s, round(float((mu_now - mu_then).abs().mean()), 6),
+                                   round(rec.psnr(vol_gt), 3)))
+                tables_then = rec.field.export(nh.PART_HASH)
+                nh.query_points(rec.field, xyz, mu_then)
+        out["arms"][norm_name] = {"series": series,
+                                  "mean_variation": round(float(np.mean([v for _, v, _ in series])), 6)}
+    print(json.dumps(out))
+
+
 def run_fftmask(args):
     """FFT channel masking (Sec. 2.3) on the benchmark scan: the same initialisation
     and batches trained with no mask, and with the mask chosen from the hash
@@ -859,6 +908,9 @@ def main():
     elif args.experiment == "ablation":
         if rank == 0:
             run_ablation(args)
+    elif args.experiment == "variation":
+        if rank == 0:
+            run_variation(args)
     elif args.impl == "reference":
         run_reference(args, rank, world)
     else:
