@@ -403,16 +403,16 @@ __device__ __forceinline__ void nhe_backward_scatter(const FieldArgs& fa, const 
 }
 
 // Gather of one sample per lane for the training kernels, with the level loop kept
-// rolled two levels at a time: each level's two features go to the lane's row of a
-// 32 x 32 float tile of the warp's scratch (swizzled float4 groups, as the stage
-// tile) and the whole row is read back at the end. Rolled, the gather is a fraction
-// of the fully unrolled code with fewer registers live, which made the fused
-// training kernels 5-10 % faster.
+// rolled (the 8 corner loads of a level in flight together): each level's two
+// features go to the lane's row of a 32 x 32 float tile of the warp's scratch
+// (swizzled float4 groups, as the stage tile) and the whole row is read back at the
+// end. Rolled, the gather is a fraction of the fully unrolled code with fewer
+// registers live, which made the fused training kernels 10-15 % faster.
 template <int L, typename TT>
 __device__ __forceinline__ void encode_point_rolled(const FieldArgs& fa, const void* tables, const float x[3],
                                                     float* stage, int lane, float (&h)[2 * L]) {
     const size_t T = (size_t)fa.Tmask + 1;
-#pragma unroll 2
+#pragma unroll 1
     for (int l = 0; l < L; l++) {
         uint32_t c[3];
         float w[3];
