@@ -347,6 +347,68 @@ __device__ __forceinline__ void warp_weight_grad(float* dzb, const float* stage,
     __syncwarp();
 }
 
+// Layer products of the FFMA path with the output loop rolled four outputs at a time
+// (one copy of the code per layer shape). linear_fwd_rolled: out[j] = b[j] +
+// sum_i W[j][i] in[i], the four outputs of a step parked in the lane's row of `row`
+// (swizzled float4 groups) and read back at the end. linear_bwd_data_rolled:
+// din[i] = sum_j W[j][i] dz[j] with dz read from the lane's row of `dzrow`
+// (swizzled float4 groups, as warp_weight_grad leaves it).
+template <int IN>
+__device__ __forceinline__ void linear_fwd_rolled(const float* __restrict__ sW, const float* __restrict__ sb,
+                                                  const float (&in)[IN], float (&out)[kW], float* row, int lane) {
+#pragma unroll 1
+    for (int jq = 0; jq < kW / 4; jq++) {
+        float acc[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            const int j = 4 * jq + e;
+            float a = sb[j];
+#pragma unroll
+            for (int i = 0; i < IN; i += 4) {
+                const float4 w = *reinterpret_cast<const float4*>(sW + j * IN + i);
+                a = fmaf(w.x, in[i], a);
+                a = fmaf(w.y, in[i + 1], a);
+                a = fmaf(w.z, in[i + 2], a);
+                a = fmaf(w.w, in[i + 3], a);
+            }
+            acc[e] = a;
+        }
+        *reinterpret_cast<float4*>(row + swz(lane, 4 * jq)) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+    }
+#pragma unroll
+    for (int q = 0; q < kW / 4; q++) {
+        const float4 v = *reinterpret_cast<const float4*>(row + swz(lane, 4 * q));
+        out[4 * q] = v.x;
+        out[4 * q + 1] = v.y;
+        out[4 * q + 2] = v.z;
+        out[4 * q + 3] = v.w;
+    }
+}
+
+template <int IN>
+__device__ __forceinline__ void linear_bwd_data_rolled(const float* __restrict__ sW, const float* dzrow, int lane,
+                                                       float (&din)[IN]) {
+#pragma unroll
+    for (int i = 0; i < IN; i++) din[i] = 0.f;
+#pragma unroll 1
+    for (int jq = 0; jq < kW / 4; jq++) {
+        const float4 d4 = *reinterpret_cast<const float4*>(dzrow + swz(lane, 4 * jq));
+        const float d[4] = {d4.x, d4.y, d4.z, d4.w};
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            const int j = 4 * jq + e;
+#pragma unroll
+            for (int i = 0; i < IN; i += 4) {
+                const float4 w = *reinterpret_cast<const float4*>(sW + j * IN + i);
+                din[i] = fmaf(w.x, d[e], din[i]);
+                din[i + 1] = fmaf(w.y, d[e], din[i + 1]);
+                din[i + 2] = fmaf(w.z, d[e], din[i + 2]);
+                din[i + 3] = fmaf(w.w, d[e], din[i + 3]);
+            }
+        }
+    }
+}
+
 // Normalized Hash Encoder backward and the hash scatter of one sample per lane.
 // dh enters as dL/dy and leaves as dL/dh; gamma / beta gradients are reduced across
 // the warp through `col` (32 x 32 floats of per-warp scratch): lane s stores element
@@ -486,7 +548,7 @@ __device__ __forceinline__ void ffma_forward(const FieldArgs& fa, const float* s
     for (int k = k0; k < H; k++) {
         if (k > 0) tmem_st(tslot0 + 32 * k, a);
         float z[kW];
-        linear_fwd<kW, kW>(sp + lay.W(k), sp + lay.b(k), a, z);
+        linear_fwd_rolled<kW>(sp + lay.W(k), sp + lay.b(k), a, z, wbuf, lane);
 #pragma unroll
         for (int j = 0; j < kW; j++) a[j] = fmaxf(z[j], 0.f);
     }
@@ -549,7 +611,7 @@ __device__ __forceinline__ void ffma_backward(const FieldArgs& fa, const float* 
         }
         warp_weight_grad<kW, false>(dzb, stage, dz, nullptr, nullptr, nullptr, sg + lay.W(k), sg + lay.b(k), lane);
         float din[kW];
-        linear_bwd_data<kW, kW>(sp + lay.W(k), dz, din);
+        linear_bwd_data_rolled<kW>(sp + lay.W(k), dzb, lane, din);
 #pragma unroll
         for (int i = 0; i < kW; i++) dz[i] = ((pos >> i) & 1u) ? din[i] : 0.f;
     }
@@ -562,7 +624,7 @@ __device__ __forceinline__ void ffma_backward(const FieldArgs& fa, const float* 
     warp_weight_grad<D, true>(dzb, stage, dz, affine ? sp : nullptr, affine ? sp + D : nullptr, smask,
                               sg + lay.W(0), sg + lay.b(0), lane);
     float dh[D];
-    linear_bwd_data<D, kW>(sp + lay.W(0), dz, dh);   // dh <- dL/dy
+    linear_bwd_data_rolled<D>(sp + lay.W(0), dzb, lane, dh);   // dh <- dL/dy
     nhe_backward_scatter<D, G>(fa, sp, smask, sg, dzb, hhat, s.rstd, dh, x, active, lane);
 }
 
