@@ -210,11 +210,12 @@ def test_train_step_loss_and_gradients_match_oracle(lib, case, loss):
 
 
 @pytest.mark.parametrize("precision", [S.PREC_F32, S.PREC_BF16])
-@pytest.mark.parametrize("N", [64, 192, 300, 520])
+@pytest.mark.parametrize("N", [64, 192, 300, 512, 520])
 def test_train_step_fused_and_split_paths_match_oracle(lib, precision, N):
     """train_step runs one fused forward+loss+backward kernel when a ray has at most
     16 chunks of 32 samples (N <= 512: several rays per CTA up to 8 chunks, one ray
-    per CTA for N = 300) and separate kernels otherwise (N = 520): all
+    per CTA for N = 300 and the largest fused ray, N = 512) and separate kernels
+    otherwise (N = 520): all
     give the oracle's loss, and one step's parameter update agrees with the update the
     oracle's gradient gives."""
     cfg = field_cfg(n_levels=16, hidden_layers=4, log2_T=12, max_res=256, precision=precision,
@@ -670,3 +671,25 @@ def test_library_matches_the_stored_oracle_step(lib):
     big = np.abs(np.array(ref["grad_value"])) > 1e-2 * ref["grad_max"]   # step sign not decided by rounding
     assert big.sum() >= 8
     np.testing.assert_allclose(p[big], np.array(ref["param_after_adam"])[big], rtol=0, atol=2e-6)
+
+
+def test_many_short_rays_fill_every_loss_partial(lib):
+    """A batch larger than the grid holds at once: 20000 rays of 8 samples (one chunk,
+    8 rays per CTA, 2500 ray groups over the persistent CTAs) gives the oracle's loss
+    and gradient."""
+    cfg = field_cfg(n_levels=8, hidden_layers=2, log2_T=12)
+    flat = S.init_params(cfg, 43, table_scale=0.5).astype(np.float32)
+    field = lib.Field(cfg, params=flat)
+    g = S.GeometryConfig(n_views=6, det_nu=200, det_nv=200)
+    geom = lib.Geometry.from_config(g)
+    og = oracle_geom(g)
+    pix = batch(g, 1, 20000, seed=5)
+    N = 8
+    a_meas = np.random.default_rng(3).uniform(0, 0.8, size=len(pix)).astype(np.float32)
+    A, cache = oracle.render_forward(flat.astype(np.float64), cfg, og, 1, pix, N)
+    ref_loss, dLdA = oracle.loss_and_grad(A, a_meas, S.LOSS_MSE)
+    ws = lib.workspace(lib.step_workspace_bytes(field, len(pix), N))
+    loss_t = torch.zeros(1, device="cuda")
+    lib.accumulate_step(field, geom, 1, _t(pix), _t(a_meas), N, loss_t, ws)
+    assert abs(_np(loss_t)[0] - ref_loss) <= 1e-5 * ref_loss
+    _grad_close(_np(field.flat_grads()), oracle.render_backward(cache, dLdA, cfg), cfg, what="many rays")
