@@ -841,9 +841,9 @@ k_ray_backward(FieldArgs fa, ViewArgs va, const int32_t* __restrict__ pix, int R
 }
 
 // ============================================================================ fused step
-// One training step for batches whose rays fit a CTA (at most kBwdWarps chunks of
-// 32 samples per ray): a CTA takes rpr whole rays at a time, warp w computing chunk
-// w % C of ray w / C. Each warp runs the forward of its samples with activations in
+// One training step for batches whose rays fit a CTA (at most kMaxFusedChunks chunks
+// of 32 samples per ray): a CTA takes rpr whole rays at a time, warp w computing
+// chunk w % C of ray w / C. Each warp runs the forward of its samples with activations in
 // tensor memory; the CTA sums each ray's chunks in order into A_r (Eq. 1), forms the
 // loss term and dL/dA_r (MSE or L1, Eq. 3) in shared memory, and every warp carries
 // on with the backward of the same samples. Ray-tile losses are accumulated in ray

@@ -64,8 +64,8 @@ cudaError_t launch_ray_loss(const float* ray_part, int R, int C, const float* a_
                             bool scale_by_loss_scale, cudaStream_t st);
 cudaError_t launch_ray_backward(const FieldArgs& fa, const ViewArgs& va, const int32_t* pix, int R,
                                 int N, const float* dLdA, cudaStream_t st);
-// Fused forward + loss + backward (rays of at most 8 chunks of 32 samples);
-// cudaErrorNotSupported for longer rays. loss_part: >= kTrainParts floats.
+// Fused forward + loss + backward (rays of at most kMaxFusedChunks chunks of 32
+// samples); cudaErrorNotSupported for longer rays. loss_part: >= kTrainParts floats.
 constexpr int kTrainParts = 4096;
 constexpr int kMaxFusedChunks = 16;   // rays of up to 16 x 32 samples take the fused kernel
 cudaError_t launch_ray_train(const FieldArgs& fa, const ViewArgs& va, const int32_t* pix, const float* a_meas,
