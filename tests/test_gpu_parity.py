@@ -606,6 +606,42 @@ def test_full_size_sampled_rays_match_oracle(lib, wname):
             _grad_close(_np(field.flat_grads()), g_ref, cfg, what=f"{wname} ray {r}", norm_rtol=tol_g)
 
 
+@pytest.mark.parametrize("wname", ["paper_fp32", "paper_bf16"])
+def test_full_size_fused_step_matches_oracle(lib, wname):
+    """The launch the benchmark times (accumulate_step: the fused kernel on 2048 rays
+    x 192 samples of the paper workload's field) against the oracle on the whole
+    batch: the loss within 1e-5 (FP32) or the mixed forward bound, every gradient
+    group within 1e-3 of its largest entry (FP32) or the mixed norm bound."""
+    w = S.WORKLOADS[wname]
+    cfg = w.field
+    flat = S.init_params(cfg, 1, table_scale=0.5).astype(np.float32)
+    field = lib.Field(cfg, params=flat)
+    geom = lib.Geometry.from_config(w.geometry)
+    og = oracle_geom(w.geometry)
+    rng = np.random.default_rng(0)
+    view = 3
+    pix = rng.choice(hit_pixels(w.geometry, view), size=w.n_rays, replace=False).astype(np.int32)
+    a_meas = rng.uniform(0.0, 0.8, size=len(pix)).astype(np.float32)
+    N = w.n_samples
+    ws = lib.workspace(lib.step_workspace_bytes(field, len(pix), N))
+    loss_t = torch.zeros(1, device="cuda")
+    lib.accumulate_step(field, geom, view, _t(pix), _t(a_meas), N, loss_t, ws)
+    info = lib.launch_info()
+    assert info["grid"] > 0 and info["tmem_cols"] == 256          # the fused kernel ran
+    ref_flat = rounded_tables(flat, cfg, cfg.precision).astype(np.float64)
+    A, cache = oracle.render_forward(ref_flat, cfg, og, view, pix, N)
+    ref_loss, dLdA = oracle.loss_and_grad(A, a_meas, S.LOSS_MSE)
+    g_ref = oracle.render_backward(cache, dLdA, cfg)
+    g = _np(field.flat_grads()) / cfg.loss_scale_init
+    if cfg.precision == S.PREC_F32:
+        assert abs(_np(loss_t)[0] - ref_loss) <= 1e-5 * ref_loss
+        _grad_close(g, g_ref, cfg, what=f"{wname} full batch")
+    else:
+        tol_f, tol_g = MIXED_TOL[cfg.precision]
+        assert abs(_np(loss_t)[0] - ref_loss) <= 2 * tol_f * ref_loss
+        _grad_close(g, g_ref, cfg, what=f"{wname} full batch", norm_rtol=tol_g)
+
+
 # ------------------------------------------------------------------------------ FFT channel mask
 def test_fft_channel_mask_matches_oracle(lib):
     """The channel mask chosen from the library's gather on the GPU (Sec. 2.3) equals
