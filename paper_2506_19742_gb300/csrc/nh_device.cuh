@@ -293,27 +293,6 @@ __device__ __forceinline__ void linear_fwd(const float* __restrict__ sW, const f
     }
 }
 
-// din[i] = sum_j W[j][i] dz[j]
-template <int IN, int OUT>
-__device__ __forceinline__ void linear_bwd_data(const float* __restrict__ sW, const float (&dz)[OUT],
-                                                float (&din)[IN]) {
-#pragma unroll
-    for (int i = 0; i < IN; i++) din[i] = 0.f;
-#pragma unroll
-    for (int j = 0; j < OUT; j++) {
-#pragma unroll
-        for (int i = 0; i < IN; i += 4) {
-            const float4 w = *reinterpret_cast<const float4*>(sW + j * IN + i);
-            din[i] = fmaf(w.x, dz[j], din[i]);
-            din[i + 1] = fmaf(w.y, dz[j], din[i + 1]);
-            din[i + 2] = fmaf(w.z, dz[j], din[i + 2]);
-            din[i + 3] = fmaf(w.w, dz[j], din[i + 3]);
-        }
-    }
-}
-
-__device__ __forceinline__ float sigmoidf_(float z) { return 1.f / (1.f + __expf(-z)); }
-
 // ----------------------------------------------------------------------------- reductions
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
