@@ -1,17 +1,20 @@
-// Field kernels of the NeRF-CBCT training step (float32 FFMA MLP), templated on the
-// table type; nh_field_{f32,bf16,f16}.cu instantiate them, nh_field.cu dispatches.
+// Field kernels of the NeRF-CBCT training step, templated on the table type (float,
+// or bf16 / f16 with the tensor-core MLP of nh_field_mma.cuh); nh_field_*.cu and
+// nh_train_*.cu instantiate them, nh_field.cu dispatches.
 //
-//  k_ray_forward   one warp per (ray, 32-sample chunk): sample -> hash gather ->
-//                  Normalized Hash Encoder -> MLP -> mu; the warp's partial of the
-//                  Beer-Lambert sum A = sum_i mu_i delta_i (Eq. 1) goes to ray_part.
-//  k_ray_loss      ray sums in fixed chunk order, MSE / L1 loss (Eq. 3) and dL/dA.
-//  k_ray_backward  recomputes the forward of each sample (features are never
-//                  stored in HBM), then MLP backward, LN backward and the hash
-//                  scatter-add (red.global.add.v2.f32); MLP / LN weight gradients
-//                  are reduced per warp and per CTA in shared memory and flushed
-//                  once per CTA.
-//  k_points        the same field at explicit points: query (forward) or the MCI
-//                  voxel-loss step (Eq. 2, forward + backward in one pass).
+//  k_ray_train     the fused training step: a CTA holds whole rays; each warp runs
+//                  sample -> hash gather -> Normalized Hash Encoder -> MLP -> mu
+//                  for 32 samples with activations in tensor memory, the CTA forms
+//                  the Beer-Lambert sums A = sum_i mu_i delta_i (Eq. 1), the loss
+//                  (Eq. 3) and dL/dA, and the same warps run the MLP backward, the
+//                  LN backward and the hash scatter-add (red.global.add.v2.f32).
+//                  MLP / LN weight gradients are reduced per warp and per CTA in
+//                  shared memory and flushed once per CTA.
+//  k_ray_forward,  the split path for rays of more than 16 chunks: forward sums,
+//  k_ray_loss,     loss, and a backward that recomputes the forward of each sample
+//  k_ray_backward  (features are never stored in HBM).
+//  k_points,       the same field at explicit points: query (forward) and the MCI
+//  k_points_fit    voxel-loss step (Eq. 2, forward + backward in one pass).
 #pragma once
 #include <cuda_runtime.h>
 
