@@ -837,6 +837,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         cpu = cpu_baseline(w, args.cpu_seconds, args.seed)
 
     if dist is not None:
+        barrier()                      # rank 0's extra measurements are done before teardown
         dist.destroy_process_group()
     if rank != 0:
         return
