@@ -55,10 +55,24 @@ def _stale() -> bool:
 
 
 def build(force: bool = False, debug: bool = False, verbose: bool = False) -> str:
-    """Compiles the CUDA sources (if changed) and links libnhcbct.so; returns its path."""
+    """Compiles the CUDA sources (if changed) and links libnhcbct.so; returns its path.
+    Processes that build at the same time (one per GPU under torchrun) take turns on
+    a file lock, so only the first one compiles."""
     if not force and not _stale():
         return LIB
+    import fcntl
     os.makedirs(BUILD, exist_ok=True)
+    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            if not force and not _stale():
+                return LIB
+            return _build_locked(debug, verbose)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(debug: bool, verbose: bool) -> str:
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(s, debug, verbose), SOURCES))
     tmp = LIB + ".tmp"
