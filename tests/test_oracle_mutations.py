@@ -1,0 +1,110 @@
+"""Mutation check of the oracle's pins (CPU only).
+
+Each mutation below plants one plausible mistake in a copy of the oracle:
+- a dropped term;
+- a wrong sign, index or constant;
+- a transposed operand.
+
+The test then runs the pin suite (tests/test_oracle_pins.py) against that copy,
+which must fail. The reproduction of the stored golden step is left out of that
+run: it was written by the oracle itself, so it pins nothing against the paper.
+A mutation that survives means a part of the oracle that no pin ties to the
+paper or to the mathematics. The mutations run as parallel
+subprocesses on copies under a temporary directory; the oracle in the repository
+is never touched.
+"""
+import os
+import shutil
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+# (name, file under oracle/, original text, mutated text); each original text
+# occurs exactly once in its file.
+MUTATIONS = [
+    ("hash primes transposed (Sec. 2.1, spatial hash)", "encoding.py",
+     "np.uint32(2654435761), np.uint32(805459861)",
+     "np.uint32(805459861), np.uint32(2654435761)"),
+    ("trilinear corner weight swapped (Sec. 2.1)", "encoding.py",
+     "(w64[:, k] if b[k] else (1.0 - w64[:, k]))",
+     "((1.0 - w64[:, k]) if b[k] else w64[:, k])"),
+    ("LayerNorm variance not normalised by the group size (Eq. 2)", "field.py",
+     "var = ((hg - mean) ** 2).mean(axis=-1, keepdims=True)",
+     "var = ((hg - mean) ** 2).sum(axis=-1, keepdims=True)"),
+    ("LayerNorm backward projection term with the wrong sign (Eq. 2)", "field.py",
+     "- hh * (dhhat * hh).mean(axis=-1, keepdims=True))",
+     "+ hh * (dhhat * hh).mean(axis=-1, keepdims=True))"),
+    ("ReLU mask of the MLP backward taken from the wrong layer", "field.py",
+     "dz = da * (zs[k - 1] > 0.0)",
+     "dz = da * (zs[k] > 0.0)"),
+    ("detector pixel centre offset dropped (Sec. 2.2)", "geometry.py",
+     "ou = ((i + f32(0.5)) - half_nu) * f32(du)",
+     "ou = (i - half_nu) * f32(du)"),
+    ("detector centre cosine and sine transposed (Sec. 2.2)", "geometry.py",
+     "0.5 - ddet * ct, 0.5 - ddet * st, 0.5,",
+     "0.5 - ddet * st, 0.5 - ddet * ct, 0.5,"),
+    ("SplitMix64 second shift off by one", "geometry.py",
+     "(z ^ (z >> np.uint64(27)))",
+     "(z ^ (z >> np.uint64(28)))"),
+    ("Beer-Lambert sum averaged instead of summed (Eq. 1)", "train.py",
+     "* delta[hit].astype(np.float64)[:, None]).sum(axis=1)",
+     "* delta[hit].astype(np.float64)[:, None]).mean(axis=1)"),
+    ("Adam first-moment bias correction dropped", "train.py",
+     "mhat = m / (1.0 - cfg.beta1 ** t)",
+     "mhat = m"),
+    ("projector voxel-centre offset dropped (Sec. 3.1)", "project.py",
+     "pc = x * f32(D) - f32(0.5)",
+     "pc = x * f32(D)"),
+    ("FFT mask statistic taken on the low band (Sec. 2.3)", "mask.py",
+     "hi = P[high].sum(axis=0)",
+     "hi = P[~high].sum(axis=0)"),
+]
+
+_IGNORE = shutil.ignore_patterns("__pycache__", "*.pyc")
+_SELF_PIN = "tests/test_oracle_pins.py::test_oracle_reproduces_its_stored_step"
+
+
+def _mutated_tree(base, idx, fname, old, new):
+    root = os.path.join(base, f"m{idx:02d}")
+    for d in ("oracle", "synthetic", "tests"):
+        shutil.copytree(os.path.join(ROOT, d), os.path.join(root, d), ignore=_IGNORE)
+    shutil.copy(os.path.join(ROOT, "pytest.ini"), root)
+    path = os.path.join(root, "oracle", fname)
+    with open(path) as f:
+        src = f.read()
+    assert src.count(old) == 1, f"mutation anchor not unique in oracle/{fname}: {old!r}"
+    with open(path, "w") as f:
+        f.write(src.replace(old, new))
+    return root
+
+
+def _pins_fail(root):
+    env = dict(os.environ, PYTHONDONTWRITEBYTECODE="1")
+    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-q", "-x",
+                        "-m", "not gpu", "-p", "no:cacheprovider", "--deselect", _SELF_PIN],
+                       cwd=root, env=env, capture_output=True, text=True, timeout=600)
+    # exit 1: a pin failed; anything else (collection or usage error) is not a caught mutation
+    return r.returncode == 1, r.stdout[-400:]
+
+
+def test_every_mutation_fails_a_pin(tmp_path):
+    roots = [_mutated_tree(str(tmp_path), i, f, o, n) for i, (_, f, o, n) in enumerate(MUTATIONS)]
+    workers = max(1, min(len(roots), (os.cpu_count() or 2) // 2))
+    with ThreadPoolExecutor(workers) as ex:
+        results = list(ex.map(_pins_fail, roots))
+    survivors = [(m[0], tail) for m, (caught, tail) in zip(MUTATIONS, results) if not caught]
+    assert not survivors, "mutations not caught by any pin:\n" + "\n".join(
+        f"- {name}\n{tail}" for name, tail in survivors)
+
+
+def test_unmutated_copy_passes(tmp_path):
+    """The copied tree itself passes the pins, so a failure above comes from the mutation."""
+    root = _mutated_tree(str(tmp_path), 0, "train.py", "mhat = m / (1.0 - cfg.beta1 ** t)",
+                         "mhat = m / (1.0 - cfg.beta1 ** t)")
+    env = dict(os.environ, PYTHONDONTWRITEBYTECODE="1")
+    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-q", "-x",
+                        "-m", "not gpu", "-p", "no:cacheprovider"],
+                       cwd=root, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout[-2000:]

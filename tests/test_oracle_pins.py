@@ -68,14 +68,23 @@ def test_dense_level_is_a_bijection():
 
 
 def test_hashed_level_special_cases_and_spread():
-    """With the x prime equal to 1, points on the x axis map to cx mod T; the index
-    stays below T; buckets of a large random sample are roughly uniform."""
+    """With the x prime equal to 1, points on the x axis map to cx mod T; on the y
+    and z axes the index is (c * pi) mod 2^32 mod T with the published per-axis
+    primes pi_2 = 2654435761 and pi_3 = 805459861 of the spatial hash (Teschner et
+    al. 2003, as used by Mueller et al. 2022), computed here in exact integers; the
+    index stays below T; buckets of a large random sample are roughly uniform."""
     n, T = 512, 1 << 10
     x = np.zeros((n, 3), dtype=np.float32)
     x[:, 0] = (np.arange(n, dtype=np.float32) + np.float32(0.25)) / np.float32(n)
     idx, _, _ = oracle.corners(x, [n], T)
     assert np.array_equal(idx[:, 0, 0], np.arange(n) % T)
     assert np.array_equal(idx[:, 0, 1], (np.arange(n) + 1) % T)
+    for axis, prime in ((1, 2654435761), (2, 805459861)):
+        xa = np.zeros((n, 3), dtype=np.float32)
+        xa[:, axis] = x[:, 0]
+        idx, _, _ = oracle.corners(xa, [n], T)
+        expect = [((c * prime) % (1 << 32)) % T for c in range(n)]
+        assert idx[:, 0, 0].tolist() == expect
     rng = np.random.default_rng(0)
     xr = rng.random((20000, 3)).astype(np.float32)
     idx, _, _ = oracle.corners(xr, [n], T)
