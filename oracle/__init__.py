@@ -21,6 +21,8 @@ transfer *gain* of Mapping Consistency Initialization, which has no closed form
 (parity unpinned; it is measured against random initialization instead). The FFT
 channel mask (mask.py) is pinned on pure tones, white noise and planted fields;
 the paper gives no grid, statistic or threshold, so those are a stated reading.
+The 3-D SSIM (ssim.py) is pinned on identical and constant volumes, on brute force
+over one window, and on a library filter.
 """
 from .geometry import view_table, ray_setup, sample_points, voxel_centres_f32, splitmix64, stratum_offsets
 from .encoding import level_resolutions, corners, encode, encode_backward
@@ -30,6 +32,7 @@ from .train import (render, loss_and_grad, render_forward, render_backward, adam
                     train_step, fit_points_step, query_points, query_volume, AdamState)
 from .project import project
 from .mask import radial_frequency, high_frequency_fraction, mask_from_fraction, channel_mask
+from .ssim import gaussian_window, ssim_map, ssim
 
 __all__ = [
     "view_table", "ray_setup", "sample_points", "voxel_centres_f32", "splitmix64", "stratum_offsets",
@@ -39,4 +42,5 @@ __all__ = [
     "render", "loss_and_grad", "render_forward", "render_backward", "adam_step",
     "train_step", "fit_points_step", "query_points", "query_volume", "AdamState",
     "project", "radial_frequency", "high_frequency_fraction", "mask_from_fraction", "channel_mask",
+    "gaussian_window", "ssim_map", "ssim",
 ]

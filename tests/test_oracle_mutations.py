@@ -60,6 +60,18 @@ MUTATIONS = [
     ("FFT mask statistic taken on the low band (Sec. 2.3)", "mask.py",
      "hi = P[high].sum(axis=0)",
      "hi = P[~high].sum(axis=0)"),
+    ("SSIM contrast constant built from K1 (Wang et al. 2004)", "ssim.py",
+     "c2 = (K2 * data_range) ** 2",
+     "c2 = (K1 * data_range) ** 2"),
+    ("SSIM Gaussian window without the factor 2 in its exponent", "ssim.py",
+     "g = np.exp(-(t * t) / (2.0 * sigma * sigma))",
+     "g = np.exp(-(t * t) / (sigma * sigma))"),
+    ("SSIM covariance factor 2 dropped", "ssim.py",
+     "((2.0 * mx * my + c1) * (2.0 * cxy + c2))",
+     "((2.0 * mx * my + c1) * (cxy + c2))"),
+    ("SSIM window not normalised to sum 1", "ssim.py",
+     "return g / g.sum()",
+     "return g / g.max()"),
 ]
 
 _IGNORE = shutil.ignore_patterns("__pycache__", "*.pyc")

@@ -482,6 +482,82 @@ def test_channel_mask_keeps_a_smooth_dense_level_and_drops_a_hashed_noise_level(
     assert frac[:2].max() < 0.1 and frac[2:].min() > 0.85
 
 
+# ---------------------------------------------------------------- 3-D SSIM (Sec. 3.2; Wang et al. 2004)
+def test_ssim_of_identical_and_of_constant_volumes():
+    """Identical volumes score 1 at every window. For constants a and b every window
+    has zero variance and covariance, so the contrast-structure factor is C2 / C2
+    and the index is the luminance term (2ab + C1) / (a^2 + b^2 + C1), C1 = 1e-4
+    at data range 1. The index is symmetric in its two volumes."""
+    rng = np.random.default_rng(3)
+    x = rng.random((14, 14, 14))
+    y = np.clip(x + 0.2 * rng.standard_normal(x.shape), 0.0, 1.0)
+    np.testing.assert_allclose(oracle.ssim_map(x, x), 1.0, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(oracle.ssim_map(x, y), oracle.ssim_map(y, x), rtol=0, atol=1e-15)
+    for a, b in ((0.0, 0.0), (0.3, 0.7), (1.0, 0.02), (0.5, 0.5)):
+        m = oracle.ssim_map(np.full((12, 12, 12), a), np.full((12, 12, 12), b))
+        assert m.shape == (2, 2, 2)
+        np.testing.assert_allclose(m, (2 * a * b + 1e-4) / (a * a + b * b + 1e-4), rtol=1e-12, atol=0)
+    # a data range of 2 scales both constants by 4
+    m = oracle.ssim_map(np.full((11, 11, 11), 0.3), np.full((11, 11, 11), 0.9), data_range=2.0)
+    np.testing.assert_allclose(m, (2 * 0.27 + 4e-4) / (0.09 + 0.81 + 4e-4), rtol=1e-12, atol=0)
+
+
+def test_ssim_matches_brute_force_window_and_a_library_filter():
+    """One window (D = 11) summed voxel by voxel with the Gaussian written out, and
+    a larger volume whose window statistics come from scipy's separable 1-D filter
+    along each axis, with variances from E[x^2] - E[x]^2: both equal the oracle's
+    direct window sums."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    rng = np.random.default_rng(4)
+    x = rng.random((11, 11, 11))
+    y = 0.5 * x + 0.5 * rng.random((11, 11, 11))
+    wsum, sx, sy, sxx, syy, sxy = 0.0, 0.0, 0.0, 0.0, 0.0, 0.0
+    for k in range(11):
+        for j in range(11):
+            for i in range(11):
+                w = math.exp(-((i - 5) ** 2 + (j - 5) ** 2 + (k - 5) ** 2) / 4.5)
+                a, b = x[k, j, i], y[k, j, i]
+                wsum += w
+                sx, sy, sxx, syy, sxy = sx + w * a, sy + w * b, sxx + w * a * a, syy + w * b * b, sxy + w * a * b
+    mx, my = sx / wsum, sy / wsum
+    vx, vy, cxy = sxx / wsum - mx * mx, syy / wsum - my * my, sxy / wsum - mx * my
+    c1, c2 = 0.01 ** 2, 0.03 ** 2
+    brute = (2 * mx * my + c1) * (2 * cxy + c2) / ((mx * mx + my * my + c1) * (vx + vy + c2))
+    got = oracle.ssim_map(x, y)
+    assert got.shape == (1, 1, 1)
+    assert abs(got[0, 0, 0] - brute) < 1e-12
+
+    D = 23
+    x = rng.random((D, D, D))
+    y = np.clip(0.8 * x + 0.1 + 0.1 * rng.standard_normal((D, D, D)), 0.0, 1.0)
+    g = np.exp(-np.arange(-5, 6) ** 2 / 4.5)
+    g /= g.sum()
+
+    def smooth(v):
+        for axis in range(3):
+            v = ndimage.correlate1d(v, g, axis=axis, mode="constant")
+        return v[5:-5, 5:-5, 5:-5]
+    mx, my = smooth(x), smooth(y)
+    vx, vy, cxy = smooth(x * x) - mx * mx, smooth(y * y) - my * my, smooth(x * y) - mx * my
+    lib = (2 * mx * my + c1) * (2 * cxy + c2) / ((mx * mx + my * my + c1) * (vx + vy + c2))
+    np.testing.assert_allclose(oracle.ssim_map(x, y), lib, rtol=0, atol=1e-12)
+
+
+def test_ssim_falls_with_noise_and_vanishes_for_independent_volumes():
+    """More additive noise on a smooth volume gives a strictly lower score; two
+    independent uniform volumes share no structure, so the covariance term, and
+    with it the score, is near 0 (C2 / (2 var + C2) ~ 0.005 per window)."""
+    D = 24
+    z, y, x = np.meshgrid(*(np.arange(D) / D,) * 3, indexing="ij")
+    smooth = 0.5 + 0.4 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y) * np.sin(np.pi * z)
+    noise = np.random.default_rng(5).standard_normal((D, D, D))
+    scores = [oracle.ssim(smooth, smooth + s * noise) for s in (0.0, 0.01, 0.03, 0.1, 0.3)]
+    assert scores[0] == pytest.approx(1.0, abs=1e-13)
+    assert all(a > b for a, b in zip(scores, scores[1:]))
+    rng = np.random.default_rng(6)
+    assert abs(oracle.ssim(rng.random((D, D, D)), rng.random((D, D, D)))) < 0.05
+
+
 # ---------------------------------------------------------------- stratified jitter
 def test_splitmix64_reference_outputs_and_jittered_strata():
     """SplitMix64 started at 1234567 gives the generator's published first outputs;
