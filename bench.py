@@ -225,6 +225,7 @@ class ClockSampler:
 
 
 def source_sha():
+    """sha256 (16 hex digits) of every file of the CUDA sources."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2506_19742_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
@@ -233,15 +234,41 @@ def source_sha():
     return h.hexdigest()[:16]
 
 
+TRAIN_KERNEL_UNITS = ("nh_train_f32.cu", "nh_train_bf16.cu", "nh_train_f16.cu")
+
+
+def kernel_sha():
+    """sha256 (16 hex digits) of the training kernel's own sources: the translation
+    units that compile k_ray_train and every CUDA-source header they include,
+    followed transitively (names and contents, in name order). Kernels in other
+    translation units do not change it."""
+    csrc = os.path.join(ROOT, "paper_2506_19742_gb300", "csrc")
+    seen, todo = set(), list(TRAIN_KERNEL_UNITS)
+    while todo:
+        f = todo.pop()
+        if f in seen:
+            continue
+        seen.add(f)
+        with open(os.path.join(csrc, f)) as fh:
+            todo.extend(re.findall(r'#include "([^"/]+)"', fh.read()))
+    h = hashlib.sha256()
+    for f in sorted(seen):
+        h.update(f.encode())
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def profiled_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch from the committed ncu summary, if it matches the current sources."""
+    """DRAM bytes per launch from the committed ncu summary, if the training
+    kernel's sources are still those it profiled."""
     p = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     if not os.path.exists(p):
         return None
     txt = open(p).read()
-    m1 = re.search(r"source_sha:\s*([0-9a-f]+)", txt)
+    m1 = re.search(r"kernel_sha:\s*([0-9a-f]+)", txt)
     m2 = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    if not m1 or not m2 or m1.group(1) != source_sha():
+    if not m1 or not m2 or m1.group(1) != kernel_sha():
         return None
     return float(m2.group(1))
 
