@@ -58,7 +58,9 @@ def parse_args():
     p.add_argument("--no-psnr", action="store_true", help="skip the time-to-PSNR runs")
     p.add_argument("--no-l2", action="store_true", help="skip the gather / scatter L2 roofline probes")
     p.add_argument("--psnr-steps", type=int, default=3000, help="step cap of the time-to-PSNR runs")
-    p.add_argument("--experiment", default="", choices=["", "mci", "fftmask", "variants", "ablation", "variation"])
+    p.add_argument("--experiment", default="", choices=["", "mci", "fftmask", "variants", "ablation", "variation",
+                                                          "views"])
+    p.add_argument("--views", default="10,25,50,100", help="views: comma-separated view counts")
     p.add_argument("--variation-steps", type=int, default=1500, help="variation: training steps per arm")
     p.add_argument("--mask-step", type=int, default=500, help="fftmask: step at which the mask is chosen")
     p.add_argument("--mask-grid", type=int, default=64, help="fftmask: voxel grid of the feature spectra")
@@ -522,6 +524,7 @@ def train_arm(nh, torch, recon, cm, w, scan, seed, steps, jitter=False, mask_ste
             if t not in reached and p >= t:
                 reached[t] = (curve[-1][0], curve[-1][1])
     out.update({"final_psnr": curve[-1][2], "best_psnr": max(c[2] for c in curve),
+                "final_ssim": round(rec.ssim(vol_gt), 4),
                 "steps_to": {str(t): reached[t][0] if t in reached else None for t in (25.0, 30.0, 35.0)},
                 "seconds_to": {str(t): reached[t][1] if t in reached else None for t in (25.0, 30.0, 35.0)},
                 "ms_per_step": round(train_ms / steps, 4), "psnr_at": [c[::2] for c in curve[:: max(1, len(curve) // 12)]],
@@ -592,9 +595,63 @@ def run_ablation(args):
                 name = f"norm={norm_name} init={init} mask={'step %d' % mask if mask else 'none'}"
                 r = train_arm(nh, torch, recon, cm, w, scan, 200 + args.seed, args.psnr_steps, mask_step=mask,
                               ln_mlp=shared if init == "MCI" else None)
-                out["arms"][name] = {k: r[k] for k in ("final_psnr", "best_psnr", "steps_to", "seconds_to")}
+                out["arms"][name] = {k: r[k] for k in ("final_psnr", "best_psnr", "final_ssim", "steps_to",
+                                                       "seconds_to")}
                 at = dict((c[0], c[1]) for c in r["curve"])
                 out["arms"][name]["psnr_at_step"] = {t: at.get(t) for t in (50, 100, 200, 500, 1000)}
+    print(json.dumps(out))
+
+
+def run_views(args):
+    """Reconstruction quality against the number of projection views (Fig. 7 of
+    the paper, which scores it in SSIM on three cases). For each view count the
+    geometry keeps its detector and spreads the views evenly over 360 degrees; on
+    each of three held-out phantoms two arms train for --psnr-steps steps: the
+    plain hash encoder from random initialisation (the NAF-style baseline), and the
+    method (Normalized Hash Encoder, LN + MLP from MCI pre-training on --mci-cases
+    reconstructions at the default 50 views). Reports final 3-D SSIM and PSNR."""
+    import dataclasses
+    import torch
+    from paper_2506_19742_gb300 import build as nhbuild
+    from paper_2506_19742_gb300 import channel_mask as cm
+    from paper_2506_19742_gb300 import nhcbct as nh
+    from paper_2506_19742_gb300 import recon
+    nhbuild.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    base = S.WORKLOADS[args.workload]
+    views = [int(v) for v in args.views.split(",")]
+    cases = [200 + args.seed + c for c in range(3)]
+    w_ln = dataclasses.replace(base, field=dataclasses.replace(base.field, norm=S.NORM_LN))
+    w_plain = dataclasses.replace(base, field=dataclasses.replace(base.field, norm=S.NORM_NONE))
+    vols = []
+    for c in range(100, 100 + args.mci_cases):
+        _, rec = time_to_psnr(nh, torch, recon, w_ln, c, dev, targets=(99.0,), max_steps=args.mci_recon_steps,
+                              eval_every=args.mci_recon_steps)
+        vols.append(rec.volume(w_ln.vol_D))
+        del rec
+    shared, _ = recon.pretrain_mci(w_ln.field, vols, steps=args.mci_pretrain_steps, points_per_step=65536,
+                                   seed=args.seed)
+    del vols
+    out = {"experiment": "views", "workload": base.name, "steps": args.psnr_steps, "cases": cases,
+           "mci_cases": args.mci_cases, "ssim": "3-D, Gaussian 11^3 window, sigma 1.5, data range 1",
+           "views": {}}
+    arms = (("hash encoder, random init", w_plain, None), ("NHE + MCI", w_ln, shared))
+    for V in views:
+        row = {name: {"ssim": [], "psnr": []} for name, _, _ in arms}
+        for seed in cases:
+            geo = dataclasses.replace(base.geometry, n_views=V)
+            scan = make_scan(nh, torch, dataclasses.replace(base, geometry=geo), seed, dev)
+            for name, w, ln_mlp in arms:
+                wv = dataclasses.replace(w, geometry=geo)
+                r = train_arm(nh, torch, recon, cm, wv, scan, seed, args.psnr_steps, ln_mlp=ln_mlp)
+                row[name]["ssim"].append(r["final_ssim"])
+                row[name]["psnr"].append(r["final_psnr"])
+            del scan
+        for name in row:
+            row[name]["mean_ssim"] = round(float(np.mean(row[name]["ssim"])), 4)
+            row[name]["mean_psnr"] = round(float(np.mean(row[name]["psnr"])), 3)
+        out["views"][V] = row
     print(json.dumps(out))
 
 
@@ -939,6 +996,9 @@ def main():
     elif args.experiment == "variation":
         if rank == 0:
             run_variation(args)
+    elif args.experiment == "views":
+        if rank == 0:
+            run_views(args)
     elif args.impl == "reference":
         run_reference(args, rank, world)
     else:

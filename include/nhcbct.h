@@ -259,6 +259,29 @@ nh_status query_volume(const nh_field* f, int32_t D, float* out_dev, void* strea
 nh_status volume_mse(const float* a_dev, const float* b_dev, int64_t n, double* out_dev, void* ws,
                      size_t ws_bytes, void* stream);
 
+/* 3-D structural similarity (SSIM) of two D^3 volumes, the image-quality score
+ * reported beside PSNR (Sec. 3.2, Fig. 7 and 8), with the settings of the SSIM
+ * paper cited there (Wang, Bovik, Sheikh and Simoncelli 2004) taken to 3-D:
+ * Gaussian window of standard deviation 1.5 voxels, 11 voxels per axis,
+ * normalised to sum 1; C1 = (0.01 data_range)^2, C2 = (0.03 data_range)^2; the
+ * local index (2 mu_x mu_y + C1)(2 sigma_xy + C2) /
+ * ((mu_x^2 + mu_y^2 + C1)(sigma_x^2 + sigma_y^2 + C2)) at each of the M^3 window
+ * positions wholly inside the volume, M = D - 10.
+ *   x_dev, y_dev  float[D^3], [z][y][x] order, device, read only.
+ *   D             11 .. 1024.
+ *   data_range    > 0 and finite (1 for volumes in [0, 1]).
+ *   mean_dev      double[1], device: the mean local index (the reported score).
+ *   map_dev       double[M^3] [z][y][x], device, or NULL: the local index.
+ *   ws            device scratch of ssim3d_workspace_bytes(D) bytes, caller-owned,
+ *                 8-byte aligned (mean_dev and map_dev too).
+ * Computed in FP64 with a fixed summation order: deterministic for a given D.
+ * Errors: NH_ERR_INVALID_ARG (null input, D or data_range out of range),
+ * NH_ERR_ALIGNMENT, NH_ERR_SIZE_MISMATCH (workspace too small), NH_ERR_CUDA. */
+nh_status ssim3d(const float* x_dev, const float* y_dev, int32_t D, double data_range, double* mean_dev,
+                 double* map_dev, void* ws, size_t ws_bytes, void* stream);
+/* Workspace bytes for ssim3d at D (NH_ERR_INVALID_ARG outside 11 .. 1024). */
+nh_status ssim3d_workspace_bytes(int32_t D, size_t* out);
+
 /* ------------------------------------------------------------------ data synthesis
  * Forward projection of a voxel volume (the TIGRE projections of Sec. 3.1):
  * for every view and pixel, the clipped ray is cut into

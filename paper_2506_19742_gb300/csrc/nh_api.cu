@@ -11,6 +11,7 @@
 #include <new>
 #include <vector>
 
+#include "nh_eval.h"
 #include "nh_internal.h"
 
 using namespace nh;
@@ -661,6 +662,29 @@ extern "C" nh_status volume_mse(const float* a, const float* b, int64_t n, doubl
     if (ws_bytes < mse_workspace_bytes()) return fail(NH_ERR_SIZE_MISMATCH, "volume_mse: workspace needs %zu bytes",
                                                       mse_workspace_bytes());
     NH_CUDA(launch_mse(a, b, n, out_dev, ws, S(stream)), "volume_mse");
+    return NH_OK;
+}
+
+extern "C" nh_status ssim3d_workspace_bytes(int32_t D, size_t* out) {
+    if (!out) return fail(NH_ERR_INVALID_ARG, "ssim3d_workspace_bytes: null argument");
+    if (D < 2 * kSsimRadius + 1 || D > kSsimMaxD)
+        return fail(NH_ERR_INVALID_ARG, "ssim3d_workspace_bytes: D must be %d..%d", 2 * kSsimRadius + 1, kSsimMaxD);
+    *out = ssim_workspace_bytes(D);
+    return NH_OK;
+}
+
+extern "C" nh_status ssim3d(const float* x, const float* y, int32_t D, double data_range, double* mean_dev,
+                            double* map_dev, void* ws, size_t ws_bytes, void* stream) {
+    if (!x || !y || !mean_dev || !ws) return fail(NH_ERR_INVALID_ARG, "ssim3d: null argument");
+    if (D < 2 * kSsimRadius + 1 || D > kSsimMaxD)
+        return fail(NH_ERR_INVALID_ARG, "ssim3d: D must be %d..%d", 2 * kSsimRadius + 1, kSsimMaxD);
+    if (!(data_range > 0.0) || !isfinite(data_range))
+        return fail(NH_ERR_INVALID_ARG, "ssim3d: data_range must be positive and finite");
+    if (!aligned(ws, 8) || !aligned(mean_dev, 8) || (map_dev && !aligned(map_dev, 8)))
+        return fail(NH_ERR_ALIGNMENT, "ssim3d: misaligned buffer");
+    if (ws_bytes < ssim_workspace_bytes(D))
+        return fail(NH_ERR_SIZE_MISMATCH, "ssim3d: workspace needs %zu bytes", ssim_workspace_bytes(D));
+    NH_CUDA(launch_ssim3d(x, y, D, data_range, mean_dev, map_dev, ws, S(stream)), "ssim3d");
     return NH_OK;
 }
 

@@ -100,6 +100,8 @@ _SIGS = {
     "query_volume": (_I, [_P, _I, _P, _P]),
     "project": (_I, [_P, _P, _I, _I, _P, _P]),
     "volume_mse": (_I, [_P, _P, C.c_int64, _P, _P, _SZ, _P]),
+    "ssim3d": (_I, [_P, _P, _I, C.c_double, _P, _P, _P, _SZ, _P]),
+    "ssim3d_workspace_bytes": (_I, [_I, C.POINTER(_SZ)]),
     "launch_info": (_I, [C.POINTER(_I), _I]),
     "sample_rays": (_I, [_P, _I, _I, _P, _I, C.c_uint64, _P, _P, _P]),
     "hash_corners": (_I, [_P, _I, _P, _P, _P, _P]),
@@ -403,6 +405,38 @@ def volume_mse(a, b, out=None, stream=None):
     _check(load().volume_mse(_ptr(a), _ptr(b), a.numel(), _ptr(out), _ptr(ws), 8192, _stream(stream)),
            "volume_mse")
     return out
+
+
+def ssim3d_workspace_bytes(D):
+    out = _SZ()
+    _check(load().ssim3d_workspace_bytes(int(D), C.byref(out)), "ssim3d_workspace_bytes")
+    return out.value
+
+
+def ssim3d(x, y, data_range=1.0, out=None, map_out=None, stream=None):
+    """3-D SSIM (Sec. 3.2; Wang et al. 2004 settings) of two D^3 float32 CUDA volumes
+    ([z][y][x]): returns the mean local index as a float64 device tensor of one
+    element; map_out (float64, (D - 10)^3) receives the local index if given."""
+    x = _dev(x, torch.float32, "x")
+    y = _dev(y, torch.float32, "y")
+    D = x.shape[0] if x.dim() == 3 else int(round(x.numel() ** (1.0 / 3.0)))
+    if D ** 3 != x.numel() or y.numel() != x.numel():
+        raise ValueError("ssim3d: x and y must both hold D^3 voxels")
+    if map_out is not None:
+        map_out = _dev(map_out, torch.float64, "map_out")
+        if map_out.numel() != (D - 10) ** 3:
+            raise ValueError("ssim3d: map_out must hold (D - 10)^3 values")
+    out = torch.empty(1, dtype=torch.float64, device=x.device) if out is None else out
+    nb = ssim3d_workspace_bytes(D)
+    ws = torch.empty((nb + 7) // 8, dtype=torch.float64, device=x.device)
+    _check(load().ssim3d(_ptr(x), _ptr(y), D, float(data_range), _ptr(out),
+                         _ptr(map_out) if map_out is not None else None, _ptr(ws), nb, _stream(stream)), "ssim3d")
+    return out
+
+
+def ssim(vol_pred, vol_gt, data_range=1.0, stream=None):
+    """Reconstruction SSIM (Sec. 3.2) of two D^3 volumes, a Python float."""
+    return float(ssim3d(vol_pred, vol_gt, data_range, stream=stream).item())
 
 
 def launch_info():

@@ -55,6 +55,11 @@ class Reconstruction:
         D = int(round(vol_gt.numel() ** (1.0 / 3.0)))
         return nh.psnr(self.volume(D), vol_gt.reshape(-1))
 
+    def ssim(self, vol_gt):
+        """3-D SSIM (data range 1) of the field at the D^3 voxel centres of vol_gt."""
+        D = int(round(vol_gt.numel() ** (1.0 / 3.0)))
+        return nh.ssim(self.volume(D), vol_gt.reshape(-1))
+
 
 def train_to_psnr(rec: Reconstruction, batches, n_samples, vol_gt, targets=(30.0, 35.0), eval_every=50,
                   max_steps=3000):

@@ -155,3 +155,32 @@ def test_batch_validation_rejects_before_any_launch(nh):
     assert lib.field_export_bytes(h, 16, C.byref(n)) == -1
     lib.field_destroy(h)
     lib.geometry_destroy(g)
+
+
+def test_ssim_workspace_and_validation_reject_before_any_launch(nh):
+    """ssim3d's host checks: window sizes 11..1024, positive finite data range,
+    8-byte alignment, workspace size; every bad call returns before touching the
+    (fake) device pointers."""
+    lib = nh.load()
+    n = C.c_size_t()
+    for D, M in ((11, 1), (128, 118)):
+        assert lib.ssim3d_workspace_bytes(D, C.byref(n)) == 0
+        assert n.value == 8 * (5 * D * D * M + 5 * D * M * M + 1024)
+    for bad in (10, 0, -3, 1025):
+        assert lib.ssim3d_workspace_bytes(bad, C.byref(n)) == -1
+    assert lib.ssim3d_workspace_bytes(11, None) == -1
+    assert lib.ssim3d_workspace_bytes(64, C.byref(n)) == 0
+    need = n.value
+    fake = 1 << 40
+    assert lib.ssim3d(fake, fake, 64, 1.0, fake, None, fake, need - 1, None) == -3
+    assert lib.ssim3d(fake, fake, 64, 1.0, fake, fake + 4, fake, need, None) == -7
+    assert lib.ssim3d(fake, fake, 64, 1.0, fake + 4, None, fake, need, None) == -7
+    assert lib.ssim3d(fake, fake, 64, 1.0, fake, None, fake + 12, need, None) == -7
+    for dr in (0.0, -1.0, float("nan"), float("inf")):
+        assert lib.ssim3d(fake, fake, 64, dr, fake, None, fake, need, None) == -1
+    assert lib.ssim3d(fake, fake, 10, 1.0, fake, None, fake, need, None) == -1
+    assert lib.ssim3d(None, fake, 64, 1.0, fake, None, fake, need, None) == -1
+    assert lib.ssim3d(fake, fake, 64, 1.0, None, None, fake, need, None) == -1
+    buf = C.create_string_buffer(256)
+    lib.nh_last_error(buf, 256)
+    assert b"ssim3d" in buf.value
