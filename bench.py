@@ -491,11 +491,13 @@ def l2_roofline(nh, torch, geom, fields, batch, N, dev):
     return out
 
 
-def train_arm(nh, torch, recon, cm, w, scan, seed, steps, jitter=False, mask_step=0, mask_grid=64, ln_mlp=None):
+def train_arm(nh, torch, recon, cm, w, scan, seed, steps, jitter=False, mask_step=0, mask_grid=64, ln_mlp=None,
+              ssim_at=()):
     """Trains workload w on a scan from seed's initialisation for `steps` steps; PSNR
     every 50 steps (not timed). jitter: a new stratified-jitter seed every step;
     mask_step > 0: FFT channel mask chosen at the end of the 50-step block holding
-    that step (between steps, outside the timed region)."""
+    that step (between steps, outside the timed region); ssim_at: steps (multiples
+    of 50) at which the 3-D SSIM is also recorded."""
     geom, vol, a_meas_all, cands = scan
     dev = torch.device("cuda", 0)
     vol_gt = torch.from_numpy(vol.astype(np.float32).ravel()).to(dev)
@@ -520,6 +522,8 @@ def train_arm(nh, torch, recon, cm, w, scan, seed, steps, jitter=False, mask_ste
             out["high_frequency_fraction"] = [round(float(x), 3) for x in frac]
         p = rec.psnr(vol_gt)
         curve.append((min(steps, s0 + 50), round(train_ms / 1e3, 4), round(p, 3)))
+        if curve[-1][0] in ssim_at:
+            out.setdefault("ssim_at_step", {})[curve[-1][0]] = round(rec.ssim(vol_gt), 4)
         for t in (25.0, 30.0, 35.0):
             if t not in reached and p >= t:
                 reached[t] = (curve[-1][0], curve[-1][1])
@@ -594,9 +598,9 @@ def run_ablation(args):
             for mask in (0, args.mask_step):
                 name = f"norm={norm_name} init={init} mask={'step %d' % mask if mask else 'none'}"
                 r = train_arm(nh, torch, recon, cm, w, scan, 200 + args.seed, args.psnr_steps, mask_step=mask,
-                              ln_mlp=shared if init == "MCI" else None)
-                out["arms"][name] = {k: r[k] for k in ("final_psnr", "best_psnr", "final_ssim", "steps_to",
-                                                       "seconds_to")}
+                              ln_mlp=shared if init == "MCI" else None, ssim_at=(200, 500, 1000))
+                out["arms"][name] = {k: r.get(k) for k in ("final_psnr", "best_psnr", "final_ssim", "ssim_at_step",
+                                                           "steps_to", "seconds_to")}
                 at = dict((c[0], c[1]) for c in r["curve"])
                 out["arms"][name]["psnr_at_step"] = {t: at.get(t) for t in (50, 100, 200, 500, 1000)}
     print(json.dumps(out))
@@ -607,9 +611,11 @@ def run_views(args):
     the paper, which scores it in SSIM on three cases). For each view count the
     geometry keeps its detector and spreads the views evenly over 360 degrees; on
     each of three held-out phantoms two arms train for --psnr-steps steps: the
-    plain hash encoder from random initialisation (the NAF-style baseline), and the
-    method (Normalized Hash Encoder, LN + MLP from MCI pre-training on --mci-cases
-    reconstructions at the default 50 views). Reports final 3-D SSIM and PSNR."""
+    plain hash encoder from random initialisation (the NAF-style baseline), the
+    Normalized Hash Encoder from random initialisation, and the whole method (NHE
+    with LN + MLP from MCI pre-training on --mci-cases reconstructions at the
+    default 50 views). Reports 3-D SSIM at steps 200 / 500 / 1000 and at the end,
+    and the final PSNR."""
     import dataclasses
     import torch
     from paper_2506_19742_gb300 import build as nhbuild
@@ -636,21 +642,28 @@ def run_views(args):
     out = {"experiment": "views", "workload": base.name, "steps": args.psnr_steps, "cases": cases,
            "mci_cases": args.mci_cases, "ssim": "3-D, Gaussian 11^3 window, sigma 1.5, data range 1",
            "views": {}}
-    arms = (("hash encoder, random init", w_plain, None), ("NHE + MCI", w_ln, shared))
+    arms = (("hash encoder, random init", w_plain, None), ("NHE, random init", w_ln, None),
+            ("NHE + MCI", w_ln, shared))
+    checkpoints = tuple(t for t in (200, 500, 1000) if t < args.psnr_steps)
     for V in views:
-        row = {name: {"ssim": [], "psnr": []} for name, _, _ in arms}
+        row = {name: {"ssim": [], "psnr": [], "ssim_at_step": []} for name, _, _ in arms}
         for seed in cases:
             geo = dataclasses.replace(base.geometry, n_views=V)
             scan = make_scan(nh, torch, dataclasses.replace(base, geometry=geo), seed, dev)
             for name, w, ln_mlp in arms:
                 wv = dataclasses.replace(w, geometry=geo)
-                r = train_arm(nh, torch, recon, cm, wv, scan, seed, args.psnr_steps, ln_mlp=ln_mlp)
+                r = train_arm(nh, torch, recon, cm, wv, scan, seed, args.psnr_steps, ln_mlp=ln_mlp,
+                              ssim_at=checkpoints)
                 row[name]["ssim"].append(r["final_ssim"])
                 row[name]["psnr"].append(r["final_psnr"])
+                row[name]["ssim_at_step"].append(r.get("ssim_at_step", {}))
             del scan
         for name in row:
             row[name]["mean_ssim"] = round(float(np.mean(row[name]["ssim"])), 4)
             row[name]["mean_psnr"] = round(float(np.mean(row[name]["psnr"])), 3)
+            row[name]["mean_ssim_at_step"] = {
+                t: round(float(np.mean([d[t] for d in row[name]["ssim_at_step"]])), 4) for t in checkpoints
+                if all(t in d for d in row[name]["ssim_at_step"])}
         out["views"][V] = row
     print(json.dumps(out))
 
