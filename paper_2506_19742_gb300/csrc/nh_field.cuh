@@ -313,11 +313,13 @@ __device__ __forceinline__ void warp_weight_grad(float* dzb, const float* stage,
             be[t] = gamma ? beta[i] * mask[i] : 0.f;
         }
     }
-    float acc[JPL][4];
+    // acc[p][t] holds rows (2p, 2p + 1) of column t: one paired FMA updates both,
+    // each element with the same single-rounded fma as a scalar FFMA
+    float2 acc[JPL / 2][4];
 #pragma unroll
-    for (int jj = 0; jj < JPL; jj++)
+    for (int jp = 0; jp < JPL / 2; jp++)
 #pragma unroll
-        for (int t = 0; t < 4; t++) acc[jj][t] = 0.f;
+        for (int t = 0; t < 4; t++) acc[jp][t] = make_float2(0.f, 0.f);
 #pragma unroll 1
     for (int s = 0; s < 32; s++) {
         const float4 a4 = *reinterpret_cast<const float4*>(stage + swz(s, 4 * ib));
@@ -326,14 +328,18 @@ __device__ __forceinline__ void warp_weight_grad(float* dzb, const float* stage,
 #pragma unroll
             for (int t = 0; t < 4; t++) a[t] = fmaf(ga[t], a[t], be[t]);
         }
+        float2 aa[4];
+#pragma unroll
+        for (int t = 0; t < 4; t++) aa[t] = make_float2(a[t], a[t]);
 #pragma unroll
         for (int q = 0; q < JPL / 4; q++) {
             const float4 d = *reinterpret_cast<const float4*>(dzb + swz(s, 4 * (jb * (JPL / 4) + q)));
-            const float dv[4] = {d.x, d.y, d.z, d.w};
+            const float2 d01 = make_float2(d.x, d.y), d23 = make_float2(d.z, d.w);
 #pragma unroll
-            for (int e = 0; e < 4; e++)
-#pragma unroll
-                for (int t = 0; t < 4; t++) acc[4 * q + e][t] = fmaf(dv[e], a[t], acc[4 * q + e][t]);
+            for (int t = 0; t < 4; t++) {
+                acc[2 * q][t] = __ffma2_rn(d01, aa[t], acc[2 * q][t]);
+                acc[2 * q + 1][t] = __ffma2_rn(d23, aa[t], acc[2 * q + 1][t]);
+            }
         }
     }
 #pragma unroll
@@ -341,7 +347,7 @@ __device__ __forceinline__ void warp_weight_grad(float* dzb, const float* stage,
 #pragma unroll
         for (int t = 0; t < 4; t++) {
             const int j = jb * JPL + jj, i = 4 * ib + t;
-            atomicAdd(sgW + j * IN + fswz(i, j, IN), acc[jj][t]);
+            atomicAdd(sgW + j * IN + fswz(i, j, IN), (jj & 1) ? acc[jj / 2][t].y : acc[jj / 2][t].x);
         }
     float bsum = 0.f;
 #pragma unroll 8
@@ -365,16 +371,14 @@ __device__ __forceinline__ void linear_fwd_rolled(const float* __restrict__ sW, 
 #pragma unroll
         for (int e = 0; e < 4; e++) {
             const int j = 4 * jq + e;
-            float a = sb[j];
+            float2 a = make_float2(sb[j], 0.f);        // (bias + even terms, odd terms)
 #pragma unroll
             for (int i = 0; i < IN; i += 4) {
                 const float4 w = *reinterpret_cast<const float4*>(sW + j * IN + i);
-                a = fmaf(w.x, in[i], a);
-                a = fmaf(w.y, in[i + 1], a);
-                a = fmaf(w.z, in[i + 2], a);
-                a = fmaf(w.w, in[i + 3], a);
+                a = __ffma2_rn(make_float2(w.x, w.y), make_float2(in[i], in[i + 1]), a);
+                a = __ffma2_rn(make_float2(w.z, w.w), make_float2(in[i + 2], in[i + 3]), a);
             }
-            acc[e] = a;
+            acc[e] = a.x + a.y;
         }
         *reinterpret_cast<float4*>(row + swz(lane, 4 * jq)) = make_float4(acc[0], acc[1], acc[2], acc[3]);
     }
@@ -400,13 +404,16 @@ __device__ __forceinline__ void linear_bwd_data_rolled(const float* __restrict__
 #pragma unroll
         for (int e = 0; e < 4; e++) {
             const int j = 4 * jq + e;
+            const float2 dd = make_float2(d[e], d[e]);
 #pragma unroll
             for (int i = 0; i < IN; i += 4) {
                 const float4 w = *reinterpret_cast<const float4*>(sW + j * IN + i);
-                din[i] = fmaf(w.x, d[e], din[i]);
-                din[i + 1] = fmaf(w.y, d[e], din[i + 1]);
-                din[i + 2] = fmaf(w.z, d[e], din[i + 2]);
-                din[i + 3] = fmaf(w.w, d[e], din[i + 3]);
+                const float2 lo = __ffma2_rn(make_float2(w.x, w.y), dd, make_float2(din[i], din[i + 1]));
+                const float2 hi = __ffma2_rn(make_float2(w.z, w.w), dd, make_float2(din[i + 2], din[i + 3]));
+                din[i] = lo.x;
+                din[i + 1] = lo.y;
+                din[i + 2] = hi.x;
+                din[i + 3] = hi.y;
             }
         }
     }
