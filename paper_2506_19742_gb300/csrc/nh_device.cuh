@@ -275,21 +275,23 @@ __device__ __forceinline__ void ln_backward(const float (&hhat)[D], const float 
 
 // ----------------------------------------------------------------------------- MLP (FFMA)
 // out[j] = b[j] + sum_i W[j][i] in[i]; W row-major [OUT][IN] in shared memory.
+// Paired FMAs (two per instruction): one half of the pair sums the bias and the
+// even-indexed terms, the other the odd-indexed terms, in increasing i; the halves
+// are added at the end. The training kernels' rolled layer products use the same
+// order, so the forward-only kernels give the same bits.
 template <int IN, int OUT>
 __device__ __forceinline__ void linear_fwd(const float* __restrict__ sW, const float* __restrict__ sb,
                                            const float (&in)[IN], float (&out)[OUT]) {
 #pragma unroll
     for (int j = 0; j < OUT; j++) {
-        float acc = sb[j];
+        float2 acc = make_float2(sb[j], 0.f);
 #pragma unroll
         for (int i = 0; i < IN; i += 4) {
             const float4 w = *reinterpret_cast<const float4*>(sW + j * IN + i);
-            acc = fmaf(w.x, in[i], acc);
-            acc = fmaf(w.y, in[i + 1], acc);
-            acc = fmaf(w.z, in[i + 2], acc);
-            acc = fmaf(w.w, in[i + 3], acc);
+            acc = __ffma2_rn(make_float2(w.x, w.y), make_float2(in[i], in[i + 1]), acc);
+            acc = __ffma2_rn(make_float2(w.z, w.w), make_float2(in[i + 2], in[i + 3]), acc);
         }
-        out[j] = acc;
+        out[j] = acc.x + acc.y;
     }
 }
 

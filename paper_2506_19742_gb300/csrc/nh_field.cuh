@@ -371,7 +371,7 @@ __device__ __forceinline__ void linear_fwd_rolled(const float* __restrict__ sW, 
 #pragma unroll
         for (int e = 0; e < 4; e++) {
             const int j = 4 * jq + e;
-            float2 a = make_float2(sb[j], 0.f);        // (bias + even terms, odd terms)
+            float2 a = make_float2(sb[j], 0.f);        // (bias + even terms, odd terms), as linear_fwd
 #pragma unroll
             for (int i = 0; i < IN; i += 4) {
                 const float4 w = *reinterpret_cast<const float4*>(sW + j * IN + i);
