@@ -11,6 +11,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "nh_eval.h"
 #include "nh_internal.h"
 
@@ -38,6 +40,16 @@ static nh_status cuda_fail(cudaError_t e, const char* where) {
     } while (0)
 
 static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+// NVTX range over one entry point, so that a profiler timeline shows the
+// library's calls around their kernels (a no-op unless a tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define NH_RANGE(name) NvtxRange nh_range_(name)
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 extern "C" const char* nh_status_string(nh_status s) {
@@ -459,6 +471,7 @@ static nh_status run_train(nh_field* f, const nh_geometry* g, int view, int R, c
 
 extern "C" nh_status accumulate_step(nh_field* f, const nh_geometry* g, const nh_ray_batch* b, float* loss_dev,
                                      void* ws, size_t ws_bytes, void* stream) {
+    NH_RANGE("accumulate_step");
     nh_status s = check_batch(f, g, b, ws, ws_bytes, true, "accumulate_step");
     if (s != NH_OK) return s;
     if (b->n_rays == 0) {
@@ -472,6 +485,7 @@ extern "C" nh_status accumulate_step(nh_field* f, const nh_geometry* g, const nh
 
 extern "C" nh_status train_step(nh_field* f, const nh_geometry* g, const nh_ray_batch* b, float* loss_dev,
                                 void* ws, size_t ws_bytes, void* stream) {
+    NH_RANGE("train_step");
     nh_status s = check_batch(f, g, b, ws, ws_bytes, true, "train_step");
     if (s != NH_OK) return s;
     const RayWs w = ray_ws(ws, b->n_rays, b->n_samples);
@@ -482,6 +496,7 @@ extern "C" nh_status train_step(nh_field* f, const nh_geometry* g, const nh_ray_
 extern "C" nh_status train_step_host(nh_field* f, const nh_geometry* g, int32_t view, int32_t R,
                                      const int32_t* pix_host, const float* a_meas_host, int32_t N,
                                      float* loss_host, void* ws, size_t ws_bytes, void* stream) {
+    NH_RANGE("train_step_host");
     nh_ray_batch b{view, R, pix_host, a_meas_host, N};
     nh_status s = check_batch(f, g, &b, ws, ws_bytes, true, "train_step_host");
     if (s != NH_OK) return s;
@@ -500,6 +515,7 @@ extern "C" nh_status train_step_host(nh_field* f, const nh_geometry* g, int32_t 
 
 extern "C" nh_status render_forward(const nh_field* f, const nh_geometry* g, const nh_ray_batch* b, float* a_pred,
                                     void* ws, size_t ws_bytes, void* stream) {
+    NH_RANGE("render_forward");
     nh_status s = check_batch(f, g, b, ws, ws_bytes, false, "render_forward");
     if (s != NH_OK) return s;
     if (b->n_rays == 0) return NH_OK;
@@ -515,6 +531,7 @@ extern "C" nh_status render_forward(const nh_field* f, const nh_geometry* g, con
 
 extern "C" nh_status render_backward(nh_field* f, const nh_geometry* g, const nh_ray_batch* b, const float* dLdA,
                                      void* ws, size_t ws_bytes, void* stream) {
+    NH_RANGE("render_backward");
     nh_status s = check_batch(f, g, b, ws, ws_bytes, false, "render_backward");
     if (s != NH_OK) return s;
     if (b->n_rays == 0) return NH_OK;
@@ -525,6 +542,7 @@ extern "C" nh_status render_backward(nh_field* f, const nh_geometry* g, const nh
 }
 
 extern "C" nh_status optimizer_step(nh_field* f, void* stream) {
+    NH_RANGE("optimizer_step");
     if (!f) return fail(NH_ERR_INVALID_ARG, "optimizer_step: null field");
     NH_CUDA(launch_adam(f->fa, f->buf.params, f->buf.grads, f->buf.adam_m, f->buf.adam_v,
                         (int64_t)align_up(f->sizes.n_params, 4), f->desc.lr, f->desc.beta1, f->desc.beta2,
@@ -554,11 +572,13 @@ static nh_status run_fit(nh_field* f, int32_t n, const float* xyz, const float* 
 
 extern "C" nh_status fit_points_backward(nh_field* f, int32_t n, const float* xyz, const float* mu_gt,
                                          float* loss_dev, void* ws, size_t ws_bytes, void* stream) {
+    NH_RANGE("fit_points_backward");
     return run_fit(f, n, xyz, mu_gt, loss_dev, ws, ws_bytes, stream, "fit_points_backward");
 }
 
 extern "C" nh_status fit_points_step(nh_field* f, int32_t n, const float* xyz, const float* mu_gt, float* loss_dev,
                                      void* ws, size_t ws_bytes, void* stream) {
+    NH_RANGE("fit_points_step");
     nh_status s = run_fit(f, n, xyz, mu_gt, loss_dev, ws, ws_bytes, stream, "fit_points_step");
     if (s != NH_OK || n == 0) return s;
     NH_CUDA(launch_adam(f->fa, f->buf.params, f->buf.grads, f->buf.adam_m, f->buf.adam_v,
@@ -568,6 +588,7 @@ extern "C" nh_status fit_points_step(nh_field* f, int32_t n, const float* xyz, c
 }
 
 extern "C" nh_status query_points(const nh_field* f, int32_t n, const float* xyz, float* mu, void* stream) {
+    NH_RANGE("query_points");
     if (!f) return fail(NH_ERR_INVALID_ARG, "query_points: null field");
     if (n < 0) return fail(NH_ERR_INVALID_ARG, "query_points: n < 0");
     if (n == 0) return NH_OK;
@@ -577,6 +598,7 @@ extern "C" nh_status query_points(const nh_field* f, int32_t n, const float* xyz
 }
 
 extern "C" nh_status query_volume(const nh_field* f, int32_t D, float* out, void* stream) {
+    NH_RANGE("query_volume");
     if (!f || !out) return fail(NH_ERR_INVALID_ARG, "query_volume: null argument");
     if (D < 1 || D > 2048) return fail(NH_ERR_INVALID_ARG, "query_volume: D must be 1..2048");
     NH_CUDA(launch_query_volume(f->fa, D, out, S(stream)), "query_volume");
@@ -584,6 +606,7 @@ extern "C" nh_status query_volume(const nh_field* f, int32_t D, float* out, void
 }
 
 extern "C" nh_status project(const nh_geometry* g, const float* vol, int32_t D, int32_t os, float* proj, void* stream) {
+    NH_RANGE("project");
     if (!g || !vol || !proj) return fail(NH_ERR_INVALID_ARG, "project: null argument");
     if (D < 1 || D > 4096 || os < 1 || os > 64) return fail(NH_ERR_INVALID_ARG, "project: need 1 <= D <= 4096, 1 <= oversample <= 64");
     if (!aligned(vol, 4) || !aligned(proj, 4)) return fail(NH_ERR_ALIGNMENT, "project: misaligned buffer");
@@ -656,6 +679,7 @@ extern "C" nh_status probe_random_red(float* table, uint64_t n_entries, int64_t 
 
 extern "C" nh_status volume_mse(const float* a, const float* b, int64_t n, double* out_dev, void* ws,
                                 size_t ws_bytes, void* stream) {
+    NH_RANGE("volume_mse");
     if (!a || !b || !out_dev || !ws) return fail(NH_ERR_INVALID_ARG, "volume_mse: null argument");
     if (n < 1) return fail(NH_ERR_INVALID_ARG, "volume_mse: n < 1");
     if (!aligned(ws, 8) || !aligned(out_dev, 8)) return fail(NH_ERR_ALIGNMENT, "volume_mse: misaligned buffer");
@@ -675,6 +699,7 @@ extern "C" nh_status ssim3d_workspace_bytes(int32_t D, size_t* out) {
 
 extern "C" nh_status ssim3d(const float* x, const float* y, int32_t D, double data_range, double* mean_dev,
                             double* map_dev, void* ws, size_t ws_bytes, void* stream) {
+    NH_RANGE("ssim3d");
     if (!x || !y || !mean_dev || !ws) return fail(NH_ERR_INVALID_ARG, "ssim3d: null argument");
     if (D < 2 * kSsimRadius + 1 || D > kSsimMaxD)
         return fail(NH_ERR_INVALID_ARG, "ssim3d: D must be %d..%d", 2 * kSsimRadius + 1, kSsimMaxD);

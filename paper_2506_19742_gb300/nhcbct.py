@@ -194,6 +194,25 @@ class Geometry:
             self.handle = None
 
 
+CHECKPOINT_FORMAT = "nhcbct-field-1"
+
+
+def _desc_json(desc) -> str:
+    import json
+    return json.dumps({name: getattr(desc, name) for name, _ in desc._fields_}, sort_keys=True)
+
+
+def config_hash(desc) -> str:
+    """sha256 (16 hex digits) of a field description's values: checkpoints load
+    only into a field of the same description."""
+    import hashlib
+    return hashlib.sha256(_desc_json(desc).encode()).hexdigest()[:16]
+
+
+def _stream_sync(stream=None):
+    (stream if stream is not None else torch.cuda.current_stream()).synchronize()
+
+
 class Field:
     """Hash grid + Normalized Hash Encoder + MLP with its caller-owned device buffers."""
 
@@ -277,6 +296,47 @@ class Field:
 
     def flat_grads(self):
         return self.grads[: self.n_params]
+
+    # ------------------------------------------------------------ checkpoint / resume
+    def save(self, path, stream=None):
+        """Writes a checkpoint (.npz): the field description and its hash, the
+        parameters, both Adam moments and the device state block (Adam step count,
+        loss scale and its growth counter, channel mask). Gradients are not kept:
+        a checkpoint is taken between steps. load() of it resumes training with the
+        same bits."""
+        import numpy as np
+        _stream_sync(stream)
+        np.savez(path, format=np.array(CHECKPOINT_FORMAT), config=np.array(_desc_json(self.desc)),
+                 config_hash=np.array(config_hash(self.desc)),
+                 params=self.params[: self.n_params].cpu().numpy(),
+                 adam_m=self.adam_m[: self.n_params].cpu().numpy(),
+                 adam_v=self.adam_v[: self.n_params].cpu().numpy(),
+                 state=self.state.cpu().numpy())
+
+    def load(self, path, stream=None):
+        """Restores a checkpoint written by save() into this field, which must have
+        been created with the same description (checked by its hash). Zeroes the
+        gradients and refreshes the 16-bit table copy."""
+        import numpy as np
+        with np.load(path) as z:
+            if str(z["format"]) != CHECKPOINT_FORMAT:
+                raise ValueError(f"{path}: not a {CHECKPOINT_FORMAT} checkpoint")
+            if str(z["config_hash"]) != config_hash(self.desc):
+                raise ValueError(f"{path}: checkpoint of another field description: {z['config']}")
+            n = self.n_params
+            for name, buf in (("params", self.params), ("adam_m", self.adam_m), ("adam_v", self.adam_v)):
+                a = z[name]
+                if a.shape != (n,) or a.dtype != np.float32:
+                    raise ValueError(f"{path}: {name} holds {a.shape} {a.dtype}, need ({n},) float32")
+                buf[:n].copy_(torch.from_numpy(a).to(buf.device))
+            st = z["state"]
+            if st.shape != tuple(self.state.shape) or st.dtype != np.float32:
+                raise ValueError(f"{path}: state block of another layout")
+            self.state.copy_(torch.from_numpy(st).to(self.state.device))
+        self.grads.zero_()
+        if self.tables_lp is not None:
+            self.refresh_lowp(stream)
+        _stream_sync(stream)
 
     def __del__(self):
         if getattr(self, "handle", None) and _lib is not None:

@@ -184,3 +184,19 @@ def test_ssim_workspace_and_validation_reject_before_any_launch(nh):
     buf = C.create_string_buffer(256)
     lib.nh_last_error(buf, 256)
     assert b"ssim3d" in buf.value
+
+
+def test_checkpoint_config_hash_tracks_the_field_description(nh):
+    """Checkpoints load only into a field of the same description: the hash is a
+    pure function of the description's values and changes with any of them."""
+    import dataclasses
+    f = S.WORKLOADS["tiny_fp32"].field
+    h0 = nh.config_hash(_fdesc(nh, f))
+    assert h0 == nh.config_hash(_fdesc(nh, dataclasses.replace(f)))
+    assert len(h0) == 16 and int(h0, 16) >= 0
+    seen = {h0}
+    for change in (dict(log2_T=15), dict(n_levels=4), dict(norm=S.NORM_NONE), dict(precision=S.PREC_BF16),
+                   dict(lr=2e-3), dict(loss=S.LOSS_L1), dict(hidden_layers=4)):
+        h = nh.config_hash(_fdesc(nh, dataclasses.replace(f, **change)))
+        assert h not in seen, change
+        seen.add(h)
