@@ -77,7 +77,14 @@ typedef struct {
     double  vol_side_mm;             /* side of the cubic volume                */
 } nh_geometry_desc;
 
+/* Validates desc and builds the per-view table (host memory only; no device
+ * allocation). *out receives a handle owned by the caller and released with
+ * geometry_destroy. Errors (NH_ERR_INVALID_ARG): a null argument; n_views < 1;
+ * a detector size outside 1..65536; a non-positive side, distance or pitch;
+ * dsd <= dso; a non-finite angle; a source inside the volume's circumscribed
+ * sphere (dso <= side * sqrt(3) / 2). */
 nh_status geometry_create(const nh_geometry_desc* desc, nh_geometry** out);
+/* Releases a handle from geometry_create (NULL is ignored). */
 void      geometry_destroy(nh_geometry* g);
 /* Host copy of the per-view table: n_views rows of 12 floats (s, c, u, v), then
  * du, dv (volume units). n_floats must be >= 12 * n_views + 2. */

@@ -200,3 +200,23 @@ def test_checkpoint_config_hash_tracks_the_field_description(nh):
         h = nh.config_hash(_fdesc(nh, dataclasses.replace(f, **change)))
         assert h not in seen, change
         seen.add(h)
+
+
+def test_every_declared_function_is_documented():
+    """Each entry point of include/nhcbct.h carries its own comment block (meaning
+    of the arguments, layout, ownership, errors) directly above it, or shares the
+    block of the declaration group it belongs to."""
+    lines = open(os.path.join(ROOT, "include", "nhcbct.h")).read().splitlines()
+    decl = re.compile(r"^\s*(?:nh_status|void|int32_t|const char\*)\s+(\w+)\s*\(")
+    undocumented = []
+    for i, line in enumerate(lines):
+        m = decl.match(line)
+        if not m:
+            continue
+        j = i - 1
+        while j >= 0 and (decl.match(lines[j]) or not lines[j].strip() or lines[j].rstrip().endswith(",")
+                          or lines[j].strip().endswith(");")):
+            j -= 1
+        if j < 0 or not lines[j].rstrip().endswith("*/"):
+            undocumented.append(m.group(1))
+    assert not undocumented, undocumented
