@@ -919,12 +919,17 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if not args.no_psnr and rank == 0:
         from paper_2506_19742_gb300 import recon
         scan = (geom, vol, a_meas_all, cands)
-        r32, _ = time_to_psnr(nh, torch, recon, w, seed, dev, scan=scan, max_steps=args.psnr_steps)
+        vol_gt = torch.from_numpy(vol.astype(np.float32).ravel()).to(dev)
+        r32, rec = time_to_psnr(nh, torch, recon, w, seed, dev, scan=scan, max_steps=args.psnr_steps)
         psnr = {"fp32": {k: r32[k] for k in ("steps_to", "seconds_to", "final_psnr", "best_psnr", "steps")}}
+        psnr["fp32"]["final_ssim"] = round(rec.ssim(vol_gt), 4)
+        del rec
         if args.mixed and S.WORKLOADS[args.mixed].geometry == w.geometry:
-            rmx, _ = time_to_psnr(nh, torch, recon, S.WORKLOADS[args.mixed], seed, dev, scan=scan,
-                                  max_steps=args.psnr_steps)
+            rmx, rec = time_to_psnr(nh, torch, recon, S.WORKLOADS[args.mixed], seed, dev, scan=scan,
+                                    max_steps=args.psnr_steps)
             psnr["mixed"] = {k: rmx[k] for k in ("steps_to", "seconds_to", "final_psnr", "best_psnr", "steps")}
+            psnr["mixed"]["final_ssim"] = round(rec.ssim(vol_gt), 4)
+            del rec
             s32, smx = r32["seconds_to"].get("30.0"), rmx["seconds_to"].get("30.0")
             psnr["seconds_to_30dB_fp32_over_mixed"] = (s32 / smx) if (s32 and smx) else None
             psnr["final_psnr_delta_db"] = round(rmx["final_psnr"] - r32["final_psnr"], 3)
