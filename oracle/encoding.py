@@ -1,5 +1,8 @@
 """Multiresolution hash encoding with trilinear interpolation (oracle).
 
+Test infrastructure: only the tests, the smoke check and the benchmark's CPU legs
+use it.
+
 The paper replaces frequency encoding with hash encoding (Sec. 1), citing the
 multiresolution hash grid of Mueller et al. (Instant-NGP) and NAF, and stresses
 that each step touches only the sparse subset of table entries that the sampled

@@ -1,5 +1,8 @@
 """The field M(x, y, z): hash encoding -> Normalized Hash Encoder -> MLP (oracle).
 
+Test infrastructure: only the tests, the smoke check and the benchmark's CPU legs
+use it.
+
 Sec. 2.3 places a Layer Normalization between the hash encoder and the neural
 network so that the features keep one global mean and variance, and masks
 feature channels found to carry noise. The equation the text announces is

@@ -1,5 +1,8 @@
 """Cone-beam geometry, ray setup and sample positions (oracle).
 
+Test infrastructure: only the tests, the smoke check and the benchmark's CPU legs
+use it.
+
 The paper renders X-rays whose source and detector positions are known
 (Sec. 2.2) and samples points along each X-ray path (Sec. 2.1, Sec. 2.5), with
 one view per batch, rays per view and points per ray as in Sec. 3.1. It does

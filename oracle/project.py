@@ -1,5 +1,8 @@
 """Cone-beam forward projector (oracle), standing in for TIGRE (Sec. 3.1).
 
+Test infrastructure: only the tests, the smoke check and the benchmark's CPU legs
+use it.
+
 The paper makes its projections with the TIGRE toolbox under the NAF setting
 (Sec. 3.1). This stand-in integrates a voxel volume along the same rays as the
 training sampler: for each detector pixel, the clipped ray [near, far] is cut

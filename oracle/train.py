@@ -1,5 +1,8 @@
 """Rendering, losses, Adam and the training / pre-training steps (oracle).
 
+Test infrastructure: only the tests, the smoke check and the benchmark's CPU legs
+use it.
+
 * Beer-Lambert ray sum (Sec. 2.2, Eq. 1): A = -ln(I / I0) = sum_i mu_i delta_i,
   accumulated in float64; a ray that misses the volume has A = 0.
 * Pixel loss (Sec. 2.5, Eq. 3) is an L1 norm of A_gt - sum_i M(x_i) delta_i; the
