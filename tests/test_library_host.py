@@ -220,3 +220,67 @@ def test_every_declared_function_is_documented():
         if j < 0 or not lines[j].rstrip().endswith("*/"):
             undocumented.append(m.group(1))
     assert not undocumented, undocumented
+
+
+def test_point_stage_and_export_validation_rejects_before_any_launch(nh):
+    """Host checks of the point, stage-probe, export / import and render entry
+    points: null, negative, misaligned and undersized arguments return their status
+    codes without touching the (fake) device addresses."""
+    lib = nh.load()
+    f = S.WORKLOADS["tiny_fp32"].field
+    h = _fake_field(nh, f)
+    g = C.c_void_p()
+    assert lib.geometry_create(C.byref(_gdesc(nh, S.GeometryConfig())), C.byref(g)) == 0
+    fake = 1 << 40
+    need = C.c_size_t()
+    # voxel-loss pre-training (Eq. 2) and its workspace
+    assert lib.points_workspace_bytes(h, 4096, C.byref(need)) == 0 and need.value % 256 == 0
+    assert lib.points_workspace_bytes(h, -1, C.byref(need)) == -1
+    assert lib.points_workspace_bytes(None, 16, C.byref(need)) == -1
+    assert lib.points_workspace_bytes(h, 4096, C.byref(need)) == 0
+    for fn in (lib.fit_points_step, lib.fit_points_backward):
+        assert fn(None, 16, fake, fake, fake, fake, need.value, None) == -1
+        assert fn(h, -1, fake, fake, fake, fake, need.value, None) == -1
+        assert fn(h, 4096, None, fake, fake, fake, need.value, None) == -1
+        assert fn(h, 4096, fake + 2, fake, fake, fake, need.value, None) == -7
+        assert fn(h, 4096, fake, fake, fake, None, need.value, None) == -1
+        assert fn(h, 4096, fake, fake, fake, fake + 64, need.value, None) == -7
+        assert fn(h, 4096, fake, fake, fake, fake, need.value - 1, None) == -3
+    # queries
+    assert lib.query_points(None, 8, fake, fake, None) == -1
+    assert lib.query_points(h, -1, fake, fake, None) == -1
+    assert lib.query_points(h, 8, None, fake, None) == -1
+    assert lib.query_points(h, 0, None, None, None) == 0          # nothing to do, nothing launched
+    assert lib.query_volume(h, -4, fake, None) == -1
+    # stage probes
+    assert lib.sample_rays(None, 0, 4, fake, 16, 0, fake, fake, None) == -1
+    assert lib.sample_rays(g, 0, 4, None, 16, 0, fake, fake, None) == -1
+    assert lib.sample_rays(g, 50, 4, fake, 16, 0, fake, fake, None) == -1
+    assert lib.sample_rays(g, 0, 4, fake, 0, 0, fake, fake, None) == -1
+    assert lib.hash_corners(h, 4, None, fake, fake, None) == -1
+    assert lib.hash_corners(h, -4, fake, fake, fake, None) == -1
+    assert lib.encode_points(h, 4, fake, None, None) == -1
+    assert lib.encode_points(h, -4, fake, fake, None) == -1
+    assert lib.scatter_points(h, 4, fake, None, None) == -1
+    assert lib.scatter_points(h, -4, fake, fake, None) == -1
+    assert lib.scatter_points(h, 4, fake, fake + 8, None) == -7
+    # export / import of parts
+    n = C.c_size_t()
+    assert lib.field_export_bytes(h, 2 | 4, C.byref(n)) == 0
+    assert lib.field_export(h, 2 | 4, None, n.value, None) == -1
+    assert lib.field_export(h, 2 | 4, fake, n.value - 4, None) == -3
+    assert lib.field_import(h, 2 | 4, fake, n.value - 4, None) == -3
+    assert lib.field_export(None, 2 | 4, fake, n.value, None) == -1
+    assert lib.field_import(h, 16, fake, n.value, None) == -1
+    assert lib.field_set_channel_mask(h, None, f.n_levels * f.n_feat, None) == -1
+    mask = (C.c_float * 64)()
+    assert lib.field_set_channel_mask(h, mask, f.n_levels * f.n_feat - 1, None) == -3
+    # render_forward / render_backward share the batch checks; backward needs dL/dA
+    assert lib.step_workspace_bytes(h, 64, 32, C.byref(need)) == 0
+    ok = nh.RayBatch(0, 64, fake, fake, 32)
+    assert lib.render_forward(h, g, C.byref(ok), None, fake, need.value, None) == -1
+    assert lib.render_backward(h, g, C.byref(ok), None, fake, need.value, None) == -1
+    assert lib.render_forward(h, g, C.byref(ok), fake, fake, need.value - 1, None) == -3
+    assert lib.render_backward(h, g, C.byref(nh.RayBatch(0, 64, fake, fake, 0)), fake, fake, need.value, None) == -1
+    lib.field_destroy(h)
+    lib.geometry_destroy(g)

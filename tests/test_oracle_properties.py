@@ -86,3 +86,26 @@ def test_stratum_offsets_lie_in_their_stratum_for_any_seed(seed, N, pix):
         k = u.astype(np.float64) * 2.0 ** 24
         assert np.all(k == np.floor(k))
         np.testing.assert_array_equal(u[0], oracle.stratum_offsets(seed, pix[:1], N)[0])
+
+
+@settings(max_examples=25, deadline=None, derandomize=True, database=None)
+@given(st.integers(min_value=11, max_value=14), st.integers(min_value=0, max_value=2 ** 32 - 1),
+       st.floats(min_value=0.0, max_value=1.0), st.floats(min_value=0.0, max_value=1.0))
+def test_ssim_is_symmetric_bounded_and_one_only_for_equal_volumes(D, seed, a, noise):
+    """Any pair of volumes in [0, 1]: the local index is symmetric in its two
+    volumes and lies in [-1, 1]. A volume against itself scores 1 at every window.
+    An affine copy a x + (1 - a) / 2 (a > 0) keeps the structure term at 1, so the
+    index equals the product of the luminance and contrast terms, each <= 1."""
+    rng = np.random.default_rng(seed)
+    x = rng.random((D, D, D))
+    y = np.clip(x + noise * rng.standard_normal((D, D, D)), 0.0, 1.0)
+    m = oracle.ssim_map(x, y)
+    np.testing.assert_allclose(m, oracle.ssim_map(y, x), rtol=0, atol=1e-14)
+    assert np.all(m <= 1.0 + 1e-12) and np.all(m >= -1.0 - 1e-12)
+    np.testing.assert_allclose(oracle.ssim_map(x, x), 1.0, rtol=0, atol=1e-12)
+    if a > 1e-3:
+        z = a * x + (1.0 - a) / 2.0
+        mz = oracle.ssim_map(x, z)
+        assert np.all(mz <= 1.0 + 1e-12)
+        if abs(a - 1.0) > 1e-3:
+            assert np.all(mz < 1.0)
