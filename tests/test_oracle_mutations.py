@@ -72,6 +72,39 @@ MUTATIONS = [
     ("SSIM window not normalised to sum 1", "ssim.py",
      "return g / g.sum()",
      "return g / g.max()"),
+    ("L1 loss gradient with the wrong sign (Eq. 3)", "train.py",
+     "return float(np.mean(np.abs(r))), np.sign(r) / R",
+     "return float(np.mean(np.abs(r))), -np.sign(r) / R"),
+    ("Adam second-moment bias correction dropped", "train.py",
+     "vhat = v / (1.0 - cfg.beta2 ** t)",
+     "vhat = v"),
+    ("Adam epsilon moved inside the square root", "train.py",
+     "(np.sqrt(vhat) + cfg.adam_eps)",
+     "np.sqrt(vhat + cfg.adam_eps)"),
+    ("sigmoid derivative missing its (1 - mu) factor", "field.py",
+     "dz = (dmu * mu * (1.0 - mu))[:, None]",
+     "dz = (dmu * mu)[:, None]"),
+    ("channel mask not applied after the LN affine step (Sec. 2.3)", "field.py",
+     "y = (gamma * hhat + beta) * mask",
+     "y = (gamma * hhat + beta)"),
+    ("LN gamma gradient without the normalized features", "field.py",
+     "dgamma = np.sum(g * hhat, axis=0)",
+     "dgamma = np.sum(g, axis=0)"),
+    ("slab clip taking the nearest entry instead of the farthest", "geometry.py",
+     "near = np.where(nz, np.maximum(near, t0), near)",
+     "near = np.where(nz, np.minimum(near, t0), near)"),
+    ("sample positions at stratum starts instead of midpoints", "geometry.py",
+     "ti = (np.arange(N, dtype=np.float32) + f32(0.5))[None, :]",
+     "ti = np.arange(N, dtype=np.float32)[None, :]"),
+    ("hash scatter without the trilinear weights", "encoding.py",
+     "contrib = (w[:, l, :] * dh[:, l * F + f][:, None]).ravel()",
+     "contrib = np.broadcast_to(dh[:, l * F + f][:, None], w[:, l, :].shape).ravel()"),
+    ("projector trilinear weights swapped", "project.py",
+     "w = np.prod(np.where(b[None, :] == 1, fr, 1.0 - fr), axis=1)",
+     "w = np.prod(np.where(b[None, :] == 1, 1.0 - fr, fr), axis=1)"),
+    ("FFT mask statistic without removing each channel's mean", "mask.py",
+     "h = h - h.mean(axis=(0, 1, 2), keepdims=True)",
+     "h = h"),
 ]
 
 _IGNORE = shutil.ignore_patterns("__pycache__", "*.pyc")

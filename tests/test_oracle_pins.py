@@ -445,21 +445,24 @@ def test_projector_of_uniform_volume_is_chord_less_boundary_ramp():
 # ---------------------------------------------------------------- FFT channel masking (Sec. 2.3)
 def test_fft_high_frequency_fraction_of_tones_constants_and_white_noise():
     """Pure tones put all their power at one radius |k| = |n| / G, a constant has
-    none, and white noise spreads it evenly over the G^3 - 1 non-zero bins."""
+    none, and white noise spreads it evenly over the G^3 - 1 non-zero bins. The
+    statistic is taken on each channel's mean-free spectrum, so a constant offset
+    added to a tone leaves its fraction unchanged."""
     G = 16
     z, y, x = np.meshgrid(np.arange(G), np.arange(G), np.arange(G), indexing="ij")
     noise = np.random.default_rng(0).normal(size=(G, G, G))
     chans = [np.cos(2 * np.pi * 2 * x / G),            # |k| = 0.125
              np.cos(2 * np.pi * 6 * y / G),            # |k| = 0.375
              np.sin(2 * np.pi * (3 * x + 3 * z) / G),  # |k| = 3 sqrt(2) / 16 = 0.265
-             np.full((G, G, G), 0.7), noise]
+             np.full((G, G, G), 0.7), noise, np.cos(2 * np.pi * 6 * y / G) + 5.0]
     h = np.stack(chans, axis=-1).reshape(G ** 3, -1)
     frac = oracle.high_frequency_fraction(h, G, 0.25)
     np.testing.assert_allclose(frac[:4], [0.0, 1.0, 1.0, 0.0], atol=1e-12)
+    assert abs(frac[5] - 1.0) < 1e-12
     n_high = sum(1 for a in range(-G // 2, G // 2) for b in range(-G // 2, G // 2)
                  for c in range(-G // 2, G // 2) if (a * a + b * b + c * c) > (0.25 * G) ** 2)
     assert abs(frac[4] - n_high / (G ** 3 - 1)) < 0.03
-    np.testing.assert_array_equal(oracle.mask_from_fraction(frac, 0.85), [1, 0, 0, 1, 0])
+    np.testing.assert_array_equal(oracle.mask_from_fraction(frac, 0.85), [1, 0, 0, 1, 0, 0])
 
 
 def test_channel_mask_keeps_a_smooth_dense_level_and_drops_a_hashed_noise_level():
