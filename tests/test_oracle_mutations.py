@@ -105,6 +105,15 @@ MUTATIONS = [
     ("FFT mask statistic without removing each channel's mean", "mask.py",
      "h = h - h.mean(axis=(0, 1, 2), keepdims=True)",
      "h = h"),
+    ("one LN group and per-level groups swapped (Sec. 2.3)", "field.py",
+     "return 1 if cfg.norm == 1 else (cfg.n_levels if cfg.norm == 2 else 0), D",
+     "return cfg.n_levels if cfg.norm == 1 else (1 if cfg.norm == 2 else 0), D"),
+    ("voxel-loss gradient with the wrong sign (Eq. 2)", "train.py",
+     "grad = flatten(field_backward(p, cache, np.sign(r) / P, cfg))",
+     "grad = flatten(field_backward(p, cache, -np.sign(r) / P, cfg))"),
+    ("voxel read-out at cell corners instead of centres", "geometry.py",
+     "g = (np.arange(D, dtype=np.float32) + f32(0.5)) / f32(D)",
+     "g = np.arange(D, dtype=np.float32) / f32(D)"),
 ]
 
 _IGNORE = shutil.ignore_patterns("__pycache__", "*.pyc")

@@ -182,6 +182,22 @@ def test_detector_symmetry():
         np.testing.assert_allclose(chord, chord[::-1, :], atol=2e-6)
 
 
+def test_voxel_read_out_grid_is_centred_and_x_fastest():
+    """The read-out grid of query_volume / PSNR: D^3 voxels tiling [0, 1]^3, so the
+    points lie symmetric about the volume centre with spacing 1/D, half a voxel in
+    from each face, in [z][y][x] order (x varies fastest)."""
+    for D in (1, 2, 5, 64):
+        c = oracle.voxel_centres_f32(D).astype(np.float64)
+        assert c.shape == (D ** 3, 3)
+        np.testing.assert_allclose(c.mean(axis=0), 0.5, rtol=0, atol=1e-6)
+        np.testing.assert_allclose(c + c[::-1], 1.0, rtol=0, atol=1e-6)   # point reflection through the centre
+        np.testing.assert_allclose(c.min(axis=0), 0.5 / D, rtol=0, atol=1e-7)
+        if D > 1:
+            np.testing.assert_allclose(c[1, 0] - c[0, 0], 1.0 / D, rtol=0, atol=1e-6)
+            np.testing.assert_allclose(c[D, 1] - c[0, 1], 1.0 / D, rtol=0, atol=1e-6)
+            np.testing.assert_allclose(c[D * D, 2] - c[0, 2], 1.0 / D, rtol=0, atol=1e-6)
+
+
 def test_constant_field_gives_c_times_chord():
     """mu == c everywhere (output weights 0, bias logit(c)) turns Eq. 1 into c * chord."""
     g = S.GeometryConfig(n_views=3, det_nu=16, det_nv=16)
