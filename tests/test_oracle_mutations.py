@@ -114,6 +114,12 @@ MUTATIONS = [
     ("voxel read-out at cell corners instead of centres", "geometry.py",
      "g = (np.arange(D, dtype=np.float32) + f32(0.5)) / f32(D)",
      "g = np.arange(D, dtype=np.float32) / f32(D)"),
+    ("view angles spread over n_views - 1 intervals", "geometry.py",
+     "theta = angle0_rad + (v * span_rad) / n_views",
+     "theta = angle0_rad + (v * span_rad) / (n_views - 1)"),
+    ("level resolutions without the guard against exp() landing below N_max", "encoding.py",
+     "return [int(math.floor(base_res * math.exp(l * step) + 1e-9)) for l in range(L)]",
+     "return [int(math.floor(base_res * math.exp(l * step))) for l in range(L)]"),
 ]
 
 _IGNORE = shutil.ignore_patterns("__pycache__", "*.pyc")
