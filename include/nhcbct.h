@@ -218,20 +218,24 @@ nh_status train_step_host(nh_field* f, const nh_geometry* g, int32_t view, int32
 /* Forward only: a_pred_dev[r] = sum_i mu_i delta_i (Eq. 1). */
 nh_status render_forward(const nh_field* f, const nh_geometry* g, const nh_ray_batch* b,
                          float* a_pred_dev, void* ws, size_t ws_bytes, void* stream);
-/* render_forward for callers that cannot allocate device memory when they call:
- * for example code that runs while a CUDA graph is being captured (cudaMalloc is
- * not allowed there), plug-ins whose host framework owns every device allocation,
- * or fixed-budget real-time loops that forbid allocation after start-up. There is
- * no counterpart in the paper; it is a deployment convenience. Instead of a
- * caller workspace it uses one block of device memory built into the library:
- * 1 MiB (1048576 bytes), held on every GPU that uses the library until the process
- * exits. Batches whose scratch exceeds it (about 26000 rays at 192 samples per ray)
- * return NH_ERR_SIZE_MISMATCH and enqueue nothing. Allocates nothing itself. The
- * first call on a device looks the block's address up (cudaGetSymbolAddress) and
- * caches it; make that first call before any stream capture. All calls share the
- * block, and every value in it is written before it is read, so nothing is
- * cleared between calls; calls whose GPU work overlaps in time (other streams or
- * threads) race on it and must be serialized by the caller. */
+/* render_forward for callers that cannot allocate device memory when they call.
+ * Examples: plug-ins whose host framework owns every device allocation and hands
+ * out none; fixed-budget real-time loops that forbid allocation after start-up;
+ * latency-critical code that cannot afford cudaMalloc's implicit device-wide
+ * synchronisation. The paper has no counterpart; this is a deployment convenience.
+ * Instead of a caller workspace it uses one block of device memory built into the
+ * library: 1 MiB (1048576 bytes), held on every GPU that uses the library until the
+ * process exits. A batch whose scratch exceeds it (about 26000 rays at 192 samples
+ * per ray) returns NH_ERR_SIZE_MISMATCH; n_rays < 0 or n_samples outside 1..2^20
+ * returns NH_ERR_INVALID_ARG; neither enqueues anything. It calls no allocator. The
+ * first call on a device (and the first after that device's context is destroyed
+ * and created again, e.g. by cudaDeviceReset) looks the block's device address up
+ * with cudaGetSymbolAddress; the address is tied to the context and cached per
+ * device and context ID. Make that first call before any stream capture. All calls
+ * share the block and it keeps the last call's contents; every value in it is
+ * written before it is read, so nothing is cleared between calls. Calls whose GPU
+ * work overlaps in time (other streams or threads) race on the block and must be
+ * serialized by the caller. */
 nh_status render_forward_noalloc(const nh_field* f, const nh_geometry* g, const nh_ray_batch* b,
                                  float* a_pred_dev, void* stream);
 /* Backward only: ACCUMULATES into grads the gradient of sum_r dLdA[r] * A_r

@@ -723,40 +723,83 @@ extern "C" nh_status launch_info(int32_t* out, int32_t n) {
 // render_forward_noalloc takes its scratch from this fixed block of device memory
 // instead of a caller workspace. The block is part of the library image: every GPU
 // on which the library is used holds it until the process exits. In host code the
-// name g_fixed_ws only stands for the variable; the device address is looked up
-// with cudaGetSymbolAddress, once per device, with that device current.
+// name g_fixed_ws only stands for the variable; its device address is looked up
+// with cudaGetSymbolAddress, with the device current, once per device and context.
+// A context torn down and created again (cudaDeviceReset) loads the module again,
+// and the block may then sit at another address, so the cached address is keyed to
+// the context's unique ID and looked up afresh when that ID changes.
 constexpr size_t kFixedWsBytes = size_t(1) << 20;
 static __device__ __align__(256) unsigned char g_fixed_ws[kFixedWsBytes];
 
+namespace {
+struct FixedSlot {
+    unsigned long long ctx_id;   // context the address belongs to (0: none yet)
+    void* ptr;
+};
+// Driver calls reached through the runtime's entry-point table, so the library
+// needs no link against libcuda.
+typedef int (*CtxGetCurrentFn)(void** ctx);
+typedef int (*CtxGetIdFn)(void* ctx, unsigned long long* id);
+}  // namespace
+
 static std::mutex g_fixed_mu;
-static void* g_fixed_ptr[64];
+static FixedSlot g_fixed[64];
+static CtxGetCurrentFn g_ctx_current = nullptr;
+static CtxGetIdFn g_ctx_id = nullptr;
+static bool g_ctx_fns_looked_up = false;
+
+// ID of the calling thread's current context, or 0 when it cannot be had.
+static unsigned long long current_context_id() {
+    if (!g_ctx_fns_looked_up) {
+        g_ctx_fns_looked_up = true;
+        void* a = nullptr;
+        void* b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) == cudaSuccess &&
+            qa == cudaDriverEntryPointSuccess && qb == cudaDriverEntryPointSuccess) {
+            g_ctx_current = (CtxGetCurrentFn)a;
+            g_ctx_id = (CtxGetIdFn)b;
+        }
+        cudaGetLastError();
+    }
+    if (!g_ctx_current || !g_ctx_id) return 0;
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_current(&ctx) != 0 || !ctx || g_ctx_id(ctx, &id) != 0) return 0;
+    return id;
+}
 
 static nh_status fixed_workspace(void** out) {
     int dev = 0;
     NH_CUDA(cudaGetDevice(&dev), "render_forward_noalloc: cudaGetDevice");
     if (dev < 0 || dev >= 64) return fail(NH_ERR_UNSUPPORTED, "render_forward_noalloc: device ordinal %d >= 64", dev);
     std::lock_guard<std::mutex> lock(g_fixed_mu);
-    if (!g_fixed_ptr[dev]) {
+    const unsigned long long id = current_context_id();
+    FixedSlot& slot = g_fixed[dev];
+    if (!slot.ptr || id == 0 || slot.ctx_id != id) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_fixed_ws);
         if (e != cudaSuccess) return cuda_fail(e, "render_forward_noalloc: cudaGetSymbolAddress");
-        g_fixed_ptr[dev] = p;
+        // The lookup makes the device's primary context current if it was not yet.
+        slot.ctx_id = id != 0 ? id : current_context_id();
+        slot.ptr = p;
     }
-    *out = g_fixed_ptr[dev];
+    *out = slot.ptr;
     return NH_OK;
 }
 
 extern "C" nh_status render_forward_noalloc(const nh_field* f, const nh_geometry* g, const nh_ray_batch* b,
                                             float* a_pred, void* stream) {
     if (!f || !g || !b) return fail(NH_ERR_INVALID_ARG, "render_forward_noalloc: null handle or batch");
-    if (b->n_rays >= 0 && b->n_samples >= 1) {
-        const size_t need = ray_ws(nullptr, b->n_rays, b->n_samples).bytes;
-        if (need > kFixedWsBytes)
-            return fail(NH_ERR_SIZE_MISMATCH,
-                        "render_forward_noalloc: %d rays x %d samples need %zu bytes of scratch, the fixed block "
-                        "holds %zu; use render_forward with a caller workspace",
-                        b->n_rays, b->n_samples, need, kFixedWsBytes);
-    }
+    if (b->n_rays < 0 || b->n_samples < 1 || b->n_samples > (1 << 20))
+        return fail(NH_ERR_INVALID_ARG, "render_forward_noalloc: need n_rays >= 0 and 1 <= n_samples <= 2^20");
+    const size_t need = ray_ws(nullptr, b->n_rays, b->n_samples).bytes;
+    if (need > kFixedWsBytes)
+        return fail(NH_ERR_SIZE_MISMATCH,
+                    "render_forward_noalloc: %d rays x %d samples need %zu bytes of scratch, the fixed block "
+                    "holds %zu; use render_forward with a caller workspace",
+                    b->n_rays, b->n_samples, need, kFixedWsBytes);
     void* ws = nullptr;
     const nh_status s = fixed_workspace(&ws);
     if (s != NH_OK) return s;

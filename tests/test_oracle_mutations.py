@@ -120,6 +120,17 @@ MUTATIONS = [
     ("level resolutions without the guard against exp() landing below N_max", "encoding.py",
      "return [int(math.floor(base_res * math.exp(l * step) + 1e-9)) for l in range(L)]",
      "return [int(math.floor(base_res * math.exp(l * step))) for l in range(L)]"),
+    # The measurement model lives with the seeded input generators, which feed both
+    # sides; a path with a "/" is taken relative to the repository root.
+    ("Poisson rate I0 e^+A instead of I0 e^-A", "synthetic/__init__.py",
+     "I = rng.poisson(I0 * np.exp(-np.asarray(A_clean, dtype=np.float64)))",
+     "I = rng.poisson(I0 * np.exp(np.asarray(A_clean, dtype=np.float64)))"),
+    ("count floor max(I, 1) dropped", "synthetic/__init__.py",
+     "return (-np.log(np.maximum(I, 1) / I0)).astype(np.float32)",
+     "return (-np.log(I / I0)).astype(np.float32)"),
+    ("measured line integral not normalised by I0", "synthetic/__init__.py",
+     "return (-np.log(np.maximum(I, 1) / I0)).astype(np.float32)",
+     "return (-np.log(np.maximum(I, 1))).astype(np.float32)"),
 ]
 
 _IGNORE = shutil.ignore_patterns("__pycache__", "*.pyc")
@@ -131,10 +142,10 @@ def _mutated_tree(base, idx, fname, old, new):
     for d in ("oracle", "synthetic", "tests"):
         shutil.copytree(os.path.join(ROOT, d), os.path.join(root, d), ignore=_IGNORE)
     shutil.copy(os.path.join(ROOT, "pytest.ini"), root)
-    path = os.path.join(root, "oracle", fname)
+    path = os.path.join(root, fname) if "/" in fname else os.path.join(root, "oracle", fname)
     with open(path) as f:
         src = f.read()
-    assert src.count(old) == 1, f"mutation anchor not unique in oracle/{fname}: {old!r}"
+    assert src.count(old) == 1, f"mutation anchor not unique in {path}: {old!r}"
     with open(path, "w") as f:
         f.write(src.replace(old, new))
     return root

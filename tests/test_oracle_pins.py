@@ -606,6 +606,35 @@ def test_splitmix64_reference_outputs_and_jittered_strata():
 
 
 # ---------------------------------------------------------------- stored record
+def test_poisson_measurement_has_the_poisson_moments_and_the_count_floor():
+    """Measured projections (Sec. 3.1; the measurement model of the north-star
+    workloads): I ~ Poisson(I0 exp(-A)), A_meas = -ln(max(I, 1) / I0). The counts
+    recovered from A_meas must have the Poisson mean and variance lambda = I0 e^-A
+    (each within 5 standard errors over 200 000 draws), A_meas must centre on A
+    (delta method: bias ~ 1/(2 lambda), spread ~ 1/sqrt(lambda)), and where lambda
+    is far below one count the floor max(I, 1) caps A_meas at ln I0."""
+    I0, n = 1e5, 200_000
+    for A, seed in ((0.0, 1), (0.5, 2), (1.7, 3), (4.0, 4), (7.0, 5)):
+        lam = I0 * math.exp(-A)
+        am = S.poisson_measure(np.full(n, A), I0, seed)
+        assert am.dtype == np.float32 and am.shape == (n,)
+        counts = np.rint(I0 * np.exp(-am.astype(np.float64)))
+        se_mean = math.sqrt(lam / n)
+        se_var = math.sqrt((lam + 2.0 * lam * lam) / n)
+        assert abs(counts.mean() - lam) < 5.0 * se_mean, (A, counts.mean(), lam)
+        assert abs(counts.var() - lam) < 5.0 * se_var, (A, counts.var(), lam)
+        assert abs(float(am.astype(np.float64).mean()) - A) < 1.0 / lam + 5.0 / math.sqrt(lam * n), A
+    # lambda = I0 e^-25 ~ 1.4e-6: nearly every draw counts zero, floored to one count.
+    am = S.poisson_measure(np.full(10_000, 25.0), I0, 6)
+    assert np.all(np.isfinite(am))
+    assert float(am.max()) == float(np.float32(math.log(I0)))
+    assert np.mean(am == np.float32(math.log(I0))) > 0.999
+    # Seeded: the same seed repeats the draw, another seed does not.
+    a = np.linspace(0.0, 2.0, 1000)
+    assert np.array_equal(S.poisson_measure(a, I0, 9), S.poisson_measure(a, I0, 9))
+    assert not np.array_equal(S.poisson_measure(a, I0, 9), S.poisson_measure(a, I0, 10))
+
+
 def test_oracle_reproduces_its_stored_step():
     """tests/golden/oracle_step.json (written by tests/golden/make_golden.py from the
     oracle alone) still matches the oracle: a change to the oracle's arithmetic shows
