@@ -57,6 +57,8 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-psnr", action="store_true", help="skip the time-to-PSNR runs")
     p.add_argument("--no-l2", action="store_true", help="skip the gather / scatter L2 roofline probes")
+    p.add_argument("--large", default="large_bf16", help="large workload measured beside ('' = skip)")
+    p.add_argument("--no-mci", action="store_true", help="skip the compact MCI block of the default run")
     p.add_argument("--psnr-steps", type=int, default=3000, help="step cap of the time-to-PSNR runs")
     p.add_argument("--experiment", default="", choices=["", "mci", "fftmask", "variants", "ablation", "variation",
                                                           "views"])
@@ -325,39 +327,33 @@ def time_to_psnr(nh, torch, recon, w: S.Workload, seed, dev, targets=(25.0, 30.0
     return res, rec
 
 
-def run_mci(args):
-    """Mapping Consistency Initialization (Sec. 2.1, 2.4): reconstruct pre-training
-    phantoms with the method itself, fit one LN + MLP to those reconstructions with
-    the voxel loss (Eq. 2), then train held-out phantoms from that LN + MLP or from
-    random initialisation and compare steps / seconds to 30 and 35 dB."""
-    import torch
-    from paper_2506_19742_gb300 import build as nhbuild
-    from paper_2506_19742_gb300 import nhcbct as nh
-    from paper_2506_19742_gb300 import recon
-    nhbuild.build()
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
-    w = S.WORKLOADS[args.workload]
+def mci_experiment(nh, torch, recon, w: S.Workload, dev, cases, recon_steps, pretrain_steps, heldout, max_steps,
+                   seed):
+    """Mapping Consistency Initialization (Sec. 2.1, 2.4): reconstruct `cases`
+    pre-training phantoms (seeds 100..) with the plain FP32 method for recon_steps
+    steps, fit one LN + MLP to those reconstructions with the voxel loss (Eq. 2) for
+    pretrain_steps steps, then train `heldout` held-out phantoms (seeds 200..) from
+    that LN + MLP or from random initialisation (the same hash tables) and record
+    steps / seconds to 25, 30 and 35 dB; also the 256^3 full-volume query rate."""
     cfg = w.field
     t0 = time.perf_counter()
     vols, rec_psnr = [], []
-    for s in range(100, 100 + args.mci_cases):
-        res, rec = time_to_psnr(nh, torch, recon, w, s, dev, targets=(99.0,), max_steps=args.mci_recon_steps,
-                                eval_every=args.mci_recon_steps)
+    for s in range(100, 100 + cases):
+        res, rec = time_to_psnr(nh, torch, recon, w, s, dev, targets=(99.0,), max_steps=recon_steps,
+                                eval_every=recon_steps)
         vols.append(rec.volume(w.vol_D))
         rec_psnr.append(res["final_psnr"])
         del rec
-    shared, pre_curve = recon.pretrain_mci(cfg, vols, steps=args.mci_pretrain_steps, points_per_step=65536,
-                                           seed=args.seed)
+    shared, pre_curve = recon.pretrain_mci(cfg, vols, steps=pretrain_steps, points_per_step=65536, seed=seed)
     del vols
     rows = []
-    for s in range(200, 200 + args.mci_heldout):
+    for s in range(200, 200 + heldout):
         scan = make_scan(nh, torch, w, s, dev)
         p0 = S.init_params(cfg, s)
-        rr, _ = time_to_psnr(nh, torch, recon, w, s, dev, targets=(25.0, 30.0, 35.0), max_steps=args.psnr_steps,
+        rr, _ = time_to_psnr(nh, torch, recon, w, s, dev, targets=(25.0, 30.0, 35.0), max_steps=max_steps,
                              params=p0, scan=scan)
         rm, rec = time_to_psnr(nh, torch, recon, w, s, dev, targets=(25.0, 30.0, 35.0),
-                               max_steps=args.psnr_steps, params=p0, scan=scan, ln_mlp=shared)
+                               max_steps=max_steps, params=p0, scan=scan, ln_mlp=shared)
         rows.append({"seed": s, "random": {k: rr[k] for k in ("steps_to", "seconds_to", "final_psnr")},
                      "mci": {k: rm[k] for k in ("steps_to", "seconds_to", "final_psnr")},
                      "psnr_at": {"random": rr["curve"][:6], "mci": rm["curve"][:6]}})
@@ -378,15 +374,33 @@ def run_mci(args):
         v = [r[key]["steps_to"][t] for r in rows]
         return None if any(x is None for x in v) else float(np.mean(v))
 
-    line = {"experiment": "mci", "workload": w.name, "precision": cfg.precision,
-            "pretrain_cases": args.mci_cases, "recon_steps": args.mci_recon_steps,
-            "pretrain_recon_psnr": rec_psnr, "pretrain_steps": args.mci_pretrain_steps,
+    def mean_psnr_at(key, step):
+        v = [next((c[2] for c in r["psnr_at"][key] if c[0] == step), None) for r in rows]
+        return None if any(x is None for x in v) else round(float(np.mean(v)), 3)
+
+    return {"experiment": "mci", "workload": w.name, "precision": cfg.precision,
+            "pretrain_cases": cases, "recon_steps": recon_steps,
+            "pretrain_recon_psnr": rec_psnr, "pretrain_steps": pretrain_steps,
             "pretrain_points_per_step": 65536, "pretrain_loss": pre_curve,
-            "heldout": rows,
+            "heldout": rows, "max_steps": max_steps,
             "mean_steps_to": {t: {"random": mean_steps("random", t), "mci": mean_steps("mci", t)}
                               for t in ("25.0", "30.0", "35.0")},
+            "mean_psnr_at_step_50": {"random": mean_psnr_at("random", 50), "mci": mean_psnr_at("mci", 50)},
             "query_256_ms": q_ms, "query_points_per_s": 256 ** 3 / (q_ms / 1e3),
             "wall_seconds": time.perf_counter() - t0}
+
+
+def run_mci(args):
+    """The MCI experiment at the sizes given on the command line (see mci_experiment)."""
+    import torch
+    from paper_2506_19742_gb300 import build as nhbuild
+    from paper_2506_19742_gb300 import nhcbct as nh
+    from paper_2506_19742_gb300 import recon
+    nhbuild.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    line = mci_experiment(nh, torch, recon, S.WORKLOADS[args.workload], dev, args.mci_cases, args.mci_recon_steps,
+                          args.mci_pretrain_steps, args.mci_heldout, args.psnr_steps, args.seed)
     print(json.dumps(line))
 
 
@@ -757,6 +771,76 @@ def run_fftmask(args):
     print(json.dumps(out))
 
 
+def measure_large(nh, torch, wl: S.Workload, seed: int, K: int, W: int, dev, peaks, peak_kind):
+    """The large configuration (256^3 shell phantom, 100 views of 512^2, T = 2^21 BF16
+    tables, 8192 rays x 256 samples): its own scan and batches, K timed train_steps
+    after W warm-up steps, then the fused kernel and Adam timed alone. Here the
+    tables (128 MiB BF16 + 256 MiB FP32 master), gradient tables and Adam state
+    (1 GiB together) exceed the L2, so HBM is the bound for both kernels."""
+    geom, _, a_meas_all, cands = make_scan(nh, torch, wl, seed, dev)
+    R, N = wl.n_rays, wl.n_samples
+    rng = np.random.default_rng(seed + 3)
+    batches = []
+    for _ in range(W + K):
+        view, pix = S.pick_rays(rng, wl.geometry.n_views, cands, R)
+        batches.append((view, torch.from_numpy(pix).to(dev),
+                        torch.from_numpy(a_meas_all[view][pix].astype(np.float32)).to(dev)))
+    field = nh.Field(wl.field, params=S.init_params(wl.field, seed))
+    ws = nh.workspace(nh.step_workspace_bytes(field, R, N), dev)
+    loss = torch.zeros(1, device=dev)
+    stream = torch.cuda.current_stream()
+    for v, p, a in batches[:W]:
+        nh.train_step(field, geom, v, p, a, N, loss, ws)
+    torch.cuda.synchronize()
+    phys = torch.cuda.current_device()
+    with ClockSampler(phys) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for v, p, a in batches[W:]:
+            nh.train_step(field, geom, v, p, a, N, loss, ws)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    nk = min(K, 20)
+
+    def timed(fn):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nk)]
+        for i in range(nk):
+            evs[i][0].record(stream)
+            fn(i)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        return float(np.mean([x.elapsed_time(y) for x, y in evs]))
+
+    t_acc = timed(lambda i: nh.accumulate_step(field, geom, batches[W + i][0], batches[W + i][1],
+                                               batches[W + i][2], N, loss, ws))
+    launch = nh.launch_info()
+    t_adam = timed(lambda i: nh.optimizer_step(field))
+    f = wl.field
+    L, F = f.n_levels, f.n_feat
+    bytes_per_sample = L * 8 * F * 2 + L * 8 * F * 4      # one BF16 gather + one FP32 scatter payload
+    n_params = S.param_layout(f)["_total"][1]
+    adam_bytes = 34 * n_params                             # p, m, v, g read; p, m, v, g written; 16-bit copy
+    peak = peaks["hbm_gbs"]
+    ach = bytes_per_sample * R * N / (t_acc / 1e3) / 1e9
+    ach_adam = adam_bytes / (t_adam / 1e3) / 1e9
+    return {"workload": wl.name, "value": R * N * K / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / K,
+            "steps": K, "warmup": W, "dtype": "bf16", "clocks": clk.summary(),
+            "config": {"rays_per_step": R, "samples_per_ray": N, "levels": L, "features": F, "log2_T": f.log2_T,
+                       "resolutions": [f.base_res, f.max_res], "mlp": f"{f.hidden_layers}x{f.width}",
+                       "volume": wl.vol_D, "views": wl.geometry.n_views,
+                       "detector": [wl.geometry.det_nu, wl.geometry.det_nv]},
+            "launch_ms": {"forward+loss+backward": round(t_acc, 4), "adam": round(t_adam, 4)},
+            "launch": launch,
+            "roofline": {"kernel": "k_ray_train", "bound": "hbm", "achieved": round(ach, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(ach / peak, 4), "peak_source": f"{peak_kind} hbm_gbs",
+                         "bytes_per_sample": bytes_per_sample, "units_per_launch": R * N,
+                         "traffic": profiled_traffic("ray_train", wl.name)},
+            "adam_roofline": {"kernel": "k_adam", "bound": "hbm", "achieved": round(ach_adam, 1), "peak": peak,
+                              "unit": "GB/s", "frac": round(ach_adam / peak, 4), "bytes_per_param": 34,
+                              "params": n_params}}
+
+
 def run_ours(args, rank: int, world: int, local_rank: int):
     import torch
     from paper_2506_19742_gb300 import build as nhbuild
@@ -934,6 +1018,26 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             psnr["seconds_to_30dB_fp32_over_mixed"] = (s32 / smx) if (s32 and smx) else None
             psnr["final_psnr_delta_db"] = round(rmx["final_psnr"] - r32["final_psnr"], 3)
 
+    large = None
+    if rank == 0 and args.large and args.large != args.workload:
+        del field, ws
+        if mixed is not None:
+            del field_m, ws_m
+        torch.cuda.empty_cache()
+        large = measure_large(nh, torch, S.WORKLOADS[args.large], seed, K, W, dev, peaks, peak_kind)
+
+    mci = None
+    if rank == 0 and not args.no_mci:
+        from paper_2506_19742_gb300 import recon
+        # compact form of the MCI experiment (bench.py --experiment mci runs it at
+        # 8 + 8 cases): 4 pre-training reconstructions, 2 held-out phantoms
+        m = mci_experiment(nh, torch, recon, w, dev, cases=4, recon_steps=1000, pretrain_steps=1500, heldout=2,
+                           max_steps=1500, seed=args.seed)
+        mci = {k: m[k] for k in ("workload", "pretrain_cases", "recon_steps", "pretrain_recon_psnr",
+                                 "pretrain_steps", "max_steps", "mean_steps_to", "mean_psnr_at_step_50",
+                                 "query_points_per_s", "wall_seconds")}
+        mci["heldout"] = [{"seed": r["seed"], "random": r["random"], "mci": r["mci"]} for r in m["heldout"]]
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, args.cpu_seconds, args.seed)
@@ -958,7 +1062,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                          f"{4 * 4 * S.param_layout(f)['_total'][1] / 1e6:.0f} MB of parameter state",
                    "parallelism": f"replicas x{world}"},
         "clocks": clocks, "e2e": e2e, "gpu_launches": (4 if fused else 5) * K, "roofline": roofline, "cpu_baseline": cpu,
-        "mixed": mixed, "l2_roofline": l2, "psnr": psnr, "final_loss": losses[-1] if losses else None,
+        "mixed": mixed, "l2_roofline": l2, "psnr": psnr, "large": large, "mci": mci,
+        "final_loss": losses[-1] if losses else None,
     }
     print(json.dumps(line))
 

@@ -187,13 +187,26 @@ def voxel_centres(D: int) -> np.ndarray:
 
 
 def paint_ellipsoids(E: EllipsoidSet, D: int) -> np.ndarray:
-    """Piecewise-constant volume (D^3, [z][y][x], float64): later ellipsoids overwrite."""
-    X = voxel_centres(D)
+    """Piecewise-constant volume (D^3, [z][y][x], float64): later ellipsoids overwrite.
+    Each ellipsoid is tested only on the voxels of the cube that holds its bounding
+    sphere (radius = its largest semi-axis, plus one voxel), since no voxel outside
+    that sphere can lie inside it."""
+    g = (np.arange(D) + 0.5) / D - 0.5
     vol = np.zeros((D, D, D))
     for k in range(len(E.values)):
-        local = (X - E.centres[k]) @ E.rot[k]           # coordinates along principal axes
-        inside = np.sum((local / E.axes[k]) ** 2, axis=-1) <= 1.0
-        vol[inside] = E.values[k]
+        c, rot, ax = E.centres[k], E.rot[k], E.axes[k]
+        rad = float(ax.max()) + 1.0 / D
+        lo = np.searchsorted(g, c - rad, side="left")
+        hi = np.searchsorted(g, c + rad, side="right")
+        if np.any(hi <= lo):
+            continue
+        z, y, x = np.meshgrid(g[lo[2]:hi[2]] - c[2], g[lo[1]:hi[1]] - c[1], g[lo[0]:hi[0]] - c[0], indexing="ij")
+        q = 0.0
+        for j in range(3):                                  # coordinates along principal axis j
+            local = x * rot[0, j] + y * rot[1, j] + z * rot[2, j]
+            q = q + (local / ax[j]) ** 2
+        sub = vol[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]]
+        sub[q <= 1.0] = E.values[k]
     return vol
 
 

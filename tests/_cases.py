@@ -1,5 +1,6 @@
 """Shared builders for the parity tests: one seeded case is fed to both the CUDA
-library and the CPU oracle (inputs only; the two share no arithmetic)."""
+library and the CPU oracle (inputs only; the two share no arithmetic), and the
+tolerance helpers of the FP32 gradient comparison."""
 import dataclasses
 
 import numpy as np
@@ -75,3 +76,104 @@ def c4_subinstance(seed=11):
 
 def replace(cfg, **kw):
     return dataclasses.replace(cfg, **kw)
+
+
+def table_kink_allowance(cache, dLdA, cfg, rel=4e-6):
+    """Elementwise bound on how far a float32 implementation's hash-table gradient
+    may lie from the oracle's because a ReLU unit whose pre-activation is within
+    float32 rounding of zero took the other branch. The ReLU derivative jumps at 0,
+    so for such a unit both branches follow from the same arithmetic to within
+    rounding, and either is a correct result. A flipped unit j of layer k adds or
+    removes the gradient path through it: dL/da_{k+1,j} W_k[j, :] at the layer's
+    input, carried down to the hash tables.
+
+    A hidden unit is ambiguous when |z| <= rel * (sum_i |W_ji a_i| + |b_j|): the
+    float32 error bound of a 32-term dot product is about 32 u = 1.9e-6 of that sum
+    (u = 2^-24), and rel = 4e-6 leaves room for the error its inputs carry in. The
+    bound sums, over the ambiguous units of each sample, the magnitude of that path
+    (|dL/da_{k+1,j}| |W_k[j, :]|, then |W|, |gamma|, |hhat| and the LayerNorm
+    backward on magnitudes, with ambiguous units passing gradient), scattered with
+    the trilinear weights. It is returned as a flat vector shaped like the gradient,
+    zero outside the tables; entries no ambiguous sample reaches get none."""
+    from oracle import field as OF
+    from oracle.encoding import encode_backward
+    p, fc, hit, delta, N = cache
+    n = OF.flatten(p).size
+    if fc is None:
+        return np.zeros(n)
+    x, res, T, mask, ncache, mu, acts, zs = fc
+    Ws, bs = p["W"], p["b"]
+    H = len(Ws) - 1
+    amb = []
+    for k in range(H):
+        scale = np.abs(acts[k]) @ np.abs(Ws[k]).T + np.abs(bs[k])
+        amb.append(np.abs(zs[k]) <= rel * scale)
+    S = np.nonzero(np.any(np.stack([a.any(axis=1) for a in amb]), axis=0))[0]
+    out = np.zeros(n)
+    if len(S) == 0:
+        return out
+    dmu = np.repeat(np.asarray(dLdA, dtype=np.float64)[hit] * delta[hit].astype(np.float64), N)[S]
+    # dL/da_{k+1} (the gradient arriving at each hidden unit's output) under the
+    # oracle's branches
+    dz = (dmu * mu[S] * (1.0 - mu[S]))[:, None]
+    da_out = [None] * H
+    for k in range(H, 0, -1):
+        da = dz @ Ws[k]
+        da_out[k - 1] = da
+        dz = da * (zs[k - 1][S] > 0.0)
+    # t bounds the change of dL/da at the input of layer k, from the flips at or
+    # above layer k, carried down layer by layer
+    t = np.zeros((len(S), Ws[H].shape[1]))
+    for k in range(H - 1, -1, -1):
+        t = (t * ((zs[k][S] > 0.0) | amb[k][S]) + np.abs(da_out[k]) * amb[k][S]) @ np.abs(Ws[k])
+    G = 1 if cfg.norm == 1 else (cfg.n_levels if cfg.norm == 2 else 0)
+    D = t.shape[1]
+    gch = t * np.abs(mask)
+    if G == 0:
+        dh = gch
+    else:
+        hhat, rstd = ncache
+        dhh = (gch * np.abs(p["gamma"])).reshape(len(S), G, D // G)
+        hg = np.abs(hhat[S]).reshape(len(S), G, D // G)
+        dh = (rstd[S][:, :, None] * (dhh + dhh.mean(axis=-1, keepdims=True)
+                                      + hg * (dhh * hg).mean(axis=-1, keepdims=True))).reshape(len(S), D)
+    tables = encode_backward(x[S], dh, res, T, cfg.n_feat)
+    out[: tables.size] = tables.ravel()
+    return out
+
+
+def fp32_gradient_errors(g, g_ref, cfg, cache, dLdA, tol=1e-3):
+    """Groups whose float32 gradient misses the oracle's, for the FP32 paths.
+
+    Dense groups (gamma, beta, W_k, b_k): every entry within tol of the group's
+    largest entry. Hash tables: the entries that no ReLU-ambiguous sample reaches
+    (see table_kink_allowance) within tol of the largest table entry; every entry
+    within tol of it plus the kink allowance; and the error norm within tol of the
+    table gradient's norm. Returns {group: (max error / max |ref|, error norm /
+    ref norm)} of the failing groups, and prints every group's errors."""
+    lay = S.param_layout(cfg)
+    allow = table_kink_allowance(cache, dLdA, cfg)
+    names = ("tables", "gamma", "beta") + tuple(f"{p}{k}" for k in range(cfg.hidden_layers + 1) for p in ("W", "b"))
+    bad, report = {}, {}
+    for name in names:
+        o, n = lay[name]
+        a, b = g[o:o + n].astype(np.float64), g_ref[o:o + n]
+        scale = np.abs(b).max()
+        d = np.abs(a - b)
+        if scale == 0:
+            if d.max() > 0:
+                bad[name] = (np.inf, np.inf)
+            continue
+        err = (d.max() / scale, np.linalg.norm(a - b) / np.linalg.norm(b))
+        if name == "tables":
+            al = allow[o:o + n]
+            strict = al == 0
+            err = (d[strict].max() / scale, err[1], float(np.max(d - al) / scale), float(np.mean(~strict)))
+            ok = err[0] <= tol and err[1] <= tol and err[2] <= tol
+        else:
+            ok = err[0] <= tol
+        report[name] = tuple(f"{e:.2e}" for e in err)
+        if not ok:
+            bad[name] = err
+    print(report)
+    return bad

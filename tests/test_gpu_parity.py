@@ -13,8 +13,8 @@ import pytest
 
 import oracle
 import synthetic as S
-from _cases import (C4_SUB, C4_SUB_GEOM, C4_SUB_N, batch, c4_subinstance, field_cfg, hit_pixels, oracle_geom,
-                    replace, rounded_tables)
+from _cases import (C4_SUB, C4_SUB_GEOM, C4_SUB_N, batch, c4_subinstance, field_cfg, fp32_gradient_errors,
+                    hit_pixels, oracle_geom, replace, rounded_tables)
 
 pytestmark = pytest.mark.gpu
 
@@ -212,12 +212,13 @@ def test_train_step_loss_and_gradients_match_oracle(lib, case, loss):
 @pytest.mark.parametrize("precision", [S.PREC_F32, S.PREC_BF16])
 @pytest.mark.parametrize("N", [64, 192, 300, 512, 520])
 def test_train_step_fused_and_split_paths_match_oracle(lib, precision, N):
-    """train_step runs one fused forward+loss+backward kernel when a ray has at most
-    16 chunks of 32 samples (N <= 512: several rays per CTA up to 8 chunks, one ray
-    per CTA for N = 300 and the largest fused ray, N = 512) and separate kernels
-    otherwise (N = 520): all
-    give the oracle's loss, and one step's parameter update agrees with the update the
-    oracle's gradient gives."""
+    """accumulate_step runs one fused forward+loss+backward kernel when a ray has at
+    most 16 chunks of 32 samples (N <= 512: several rays per CTA up to 8 chunks, one
+    ray per CTA for N = 300 and the largest fused ray, N = 512) and separate kernels
+    otherwise (N = 520). Each gives the oracle's loss (FP32 within 1e-5) and every
+    gradient group element by element (FP32 within 1e-3 of the group's largest
+    entry, BF16 within the mixed norm bound); train_step then gives the same loss,
+    applies Adam and zeroes the gradients."""
     cfg = field_cfg(n_levels=16, hidden_layers=4, log2_T=12, max_res=256, precision=precision,
                     loss_scale_init=1.0)
     flat = S.init_params(cfg, 40, table_scale=0.5).astype(np.float32)
@@ -229,18 +230,26 @@ def test_train_step_fused_and_split_paths_match_oracle(lib, precision, N):
     ref_flat = rounded_tables(flat, cfg, precision).astype(np.float64)
     A, cache = oracle.render_forward(ref_flat, cfg, og, 2, pix, N)
     ref_loss, dLdA = oracle.loss_and_grad(A, a_meas, S.LOSS_MSE)
+    g_ref = oracle.render_backward(cache, dLdA, cfg)
     ws = lib.workspace(lib.step_workspace_bytes(field, len(pix), N))
+    tol_f = 1e-5 if precision == S.PREC_F32 else 2 * MIXED_TOL[precision][0]
     loss_t = torch.zeros(1, device="cuda")
+    lib.accumulate_step(field, geom, 2, _t(pix), _t(a_meas), N, loss_t, ws)
+    assert abs(_np(loss_t)[0] - ref_loss) <= tol_f * ref_loss
+    g = _np(field.flat_grads())
+    if precision == S.PREC_F32:
+        bad = fp32_gradient_errors(g, g_ref, cfg, cache, dLdA)
+        assert not bad, (f"fused/split N={N}", bad)
+    else:
+        _grad_close(g, g_ref, cfg, what=f"fused/split N={N}", norm_rtol=MIXED_TOL[precision][1])
+    field.grads.zero_()
+    loss_t.zero_()
     lib.train_step(field, geom, 2, _t(pix), _t(a_meas), N, loss_t, ws)
-    tol_f = 1e-5 if precision == S.PREC_F32 else MIXED_TOL[precision][0]
-    assert abs(_np(loss_t)[0] - ref_loss) <= 2 * tol_f * ref_loss
-    # first Adam step: p - lr * g / (|g| + eps); compare where the oracle's |g| is not tiny
-    g = oracle.render_backward(cache, dLdA, cfg)
-    step = _np(field.flat_params()).astype(np.float64) - flat.astype(np.float64)
-    big = np.abs(g) > 1e-3 * np.abs(g).max()
-    expect = -cfg.lr * g / (np.abs(g) + cfg.adam_eps)
-    agree = np.mean(np.abs(step[big] - expect[big]) < 0.1 * cfg.lr)
-    assert agree > (0.999 if precision == S.PREC_F32 else 0.97), agree
+    assert abs(_np(loss_t)[0] - ref_loss) <= tol_f * ref_loss
+    assert float(field.grads.abs().max()) == 0.0
+    flags, _, step = field.poll_status()
+    assert step == 1 and flags == 0
+    assert not np.array_equal(_np(field.flat_params()), flat)
 
 
 @pytest.mark.parametrize("N", [192, 520])
@@ -611,7 +620,8 @@ def test_full_size_fused_step_matches_oracle(lib, wname):
     """The launch the benchmark times (accumulate_step: the fused kernel on 2048 rays
     x 192 samples of the paper workload's field) against the oracle on the whole
     batch: the loss within 1e-5 (FP32) or the mixed forward bound, every gradient
-    group within 1e-3 of its largest entry (FP32) or the mixed norm bound."""
+    group within 1e-3 of its largest entry (FP32, with the ReLU-kink allowance on
+    the table entries that ambiguous samples reach) or the mixed norm bound."""
     w = S.WORKLOADS[wname]
     cfg = w.field
     flat = S.init_params(cfg, 1, table_scale=0.5).astype(np.float32)
@@ -635,7 +645,8 @@ def test_full_size_fused_step_matches_oracle(lib, wname):
     g = _np(field.flat_grads()) / cfg.loss_scale_init
     if cfg.precision == S.PREC_F32:
         assert abs(_np(loss_t)[0] - ref_loss) <= 1e-5 * ref_loss
-        _grad_close(g, g_ref, cfg, what=f"{wname} full batch")
+        bad = fp32_gradient_errors(g, g_ref, cfg, cache, dLdA)
+        assert not bad, (f"{wname} full batch", bad)
     else:
         tol_f, tol_g = MIXED_TOL[cfg.precision]
         assert abs(_np(loss_t)[0] - ref_loss) <= 2 * tol_f * ref_loss
