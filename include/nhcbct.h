@@ -162,6 +162,24 @@ nh_status field_reset_state(nh_field* f, void* stream);
 nh_status field_refresh_lowp(nh_field* f, void* stream);
 /* Channel mask m (Sec. 2.3: masking of noisy feature channels), n = L * F host floats. */
 nh_status field_set_channel_mask(nh_field* f, const float* mask_host, int32_t n, void* stream);
+/* FFT channel-mask selection (Sec. 2.3: some hash-feature channels carry noise, a
+ * Fourier transform tells them apart, and they are masked during training; the
+ * paper gives no grid, statistic or threshold). Each of the L * F channels of the
+ * hash features h (before the normalization) is sampled at the voxel centres
+ * (k + 1/2) / G of a G^3 grid, its mean over the grid removed and its 3-D DFT taken
+ * (FP64); frac_dev[c] (double[L * F]) receives the share of its power at radial
+ * frequencies |k| > cutoff (cycles per voxel; 0 for a channel without variance),
+ * and the channel's mask is 0 where frac > threshold, else 1. mask_dev (float
+ * [L * F], may be null) receives the mask; with apply != 0 it is also installed as
+ * the field's channel mask (as field_set_channel_mask, on the stream). Sums run in
+ * a fixed order: the same field gives the same fractions on every run. Supports
+ * F = 2 with L = 8 or 16 (else NH_ERR_UNSUPPORTED); 2 <= G <= 128. ws: device
+ * scratch of channel_mask_workspace_bytes(f, G) bytes (268 MB at G = 64, L * F =
+ * 32), 256-byte aligned; frac_dev 8-byte aligned. Asynchronous on the stream;
+ * allocates nothing. An occasional step between training steps. */
+nh_status channel_mask_workspace_bytes(const nh_field* f, int32_t G, size_t* out);
+nh_status field_select_channel_mask(nh_field* f, int32_t G, double cutoff, double threshold, int32_t apply,
+                                    double* frac_dev, float* mask_dev, void* ws, size_t ws_bytes, void* stream);
 nh_status field_level_resolutions(const nh_field* f, int32_t* out, int32_t n);
 /* Export / import a subset of the parameters (MCI transfers NH_PART_LN |
  * NH_PART_MLP, Sec. 2.1). The packed order is HASH, LN (gamma, beta), MLP, then,

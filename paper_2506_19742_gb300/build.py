@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnhcbct.so")
 SOURCES = ["nh_train_f32.cu", "nh_train_bf16.cu", "nh_train_f16.cu", "nh_field_f32.cu", "nh_field_bf16.cu",
            "nh_field_f16.cu", "nh_api.cu", "nh_field.cu", "nh_adam.cu", "nh_project.cu", "nh_probe.cu",
-           "nh_ssim.cu"]
+           "nh_ssim.cu", "nh_mask.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

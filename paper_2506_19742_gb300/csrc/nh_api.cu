@@ -15,6 +15,7 @@
 
 #include "nh_eval.h"
 #include "nh_internal.h"
+#include "nh_mask.h"
 
 using namespace nh;
 
@@ -294,6 +295,32 @@ extern "C" nh_status field_set_channel_mask(nh_field* f, const float* mask, int3
     NH_CUDA(cudaMemcpyAsync(f->fa.state->mask, mask, sizeof(float) * n, cudaMemcpyHostToDevice, S(stream)),
             "field_set_channel_mask");
     NH_CUDA(cudaStreamSynchronize(S(stream)), "field_set_channel_mask sync");
+    return NH_OK;
+}
+
+extern "C" nh_status channel_mask_workspace_bytes(const nh_field* f, int32_t G, size_t* out) {
+    if (!f || !out) return fail(NH_ERR_INVALID_ARG, "channel_mask_workspace_bytes: null argument");
+    if (G < 2 || G > kMaskMaxG) return fail(NH_ERR_INVALID_ARG, "channel_mask_workspace_bytes: G must be 2..%d", kMaskMaxG);
+    *out = mask_workspace_bytes(G, f->fa.D);
+    return NH_OK;
+}
+
+extern "C" nh_status field_select_channel_mask(nh_field* f, int32_t G, double cutoff, double threshold,
+                                               int32_t apply, double* frac_dev, float* mask_dev, void* ws,
+                                               size_t ws_bytes, void* stream) {
+    NH_RANGE("field_select_channel_mask");
+    if (!f || !frac_dev || !ws) return fail(NH_ERR_INVALID_ARG, "field_select_channel_mask: null argument");
+    if (G < 2 || G > kMaskMaxG) return fail(NH_ERR_INVALID_ARG, "field_select_channel_mask: G must be 2..%d", kMaskMaxG);
+    if (!(cutoff >= 0.0) || !isfinite(cutoff) || !isfinite(threshold))
+        return fail(NH_ERR_INVALID_ARG, "field_select_channel_mask: need a finite cutoff >= 0 and a finite threshold");
+    if (!mask_supported(f->fa))
+        return fail(NH_ERR_UNSUPPORTED, "field_select_channel_mask: built for F = 2 with L = 8 or 16");
+    if (!aligned(frac_dev, 8) || !aligned(mask_dev, 4) || !aligned(ws, 256))
+        return fail(NH_ERR_ALIGNMENT, "field_select_channel_mask: misaligned buffer");
+    const size_t need = mask_workspace_bytes(G, f->fa.D);
+    if (ws_bytes < need) return fail(NH_ERR_SIZE_MISMATCH, "field_select_channel_mask: workspace needs %zu bytes", need);
+    NH_CUDA(launch_select_mask(f->fa, G, cutoff, threshold, apply, frac_dev, mask_dev, ws, S(stream)),
+            "field_select_channel_mask");
     return NH_OK;
 }
 

@@ -81,6 +81,8 @@ _SIGS = {
     "field_refresh_lowp": (_I, [_P, _P]),
     "field_set_channel_mask": (_I, [_P, C.POINTER(C.c_float), _I, _P]),
     "field_level_resolutions": (_I, [_P, C.POINTER(_I), _I]),
+    "channel_mask_workspace_bytes": (_I, [_P, _I, C.POINTER(_SZ)]),
+    "field_select_channel_mask": (_I, [_P, _I, C.c_double, C.c_double, _I, _P, _P, _P, _SZ, _P]),
     "field_export_bytes": (_I, [_P, C.c_uint32, C.POINTER(_SZ)]),
     "field_export": (_I, [_P, C.c_uint32, _P, _SZ, _P]),
     "field_import": (_I, [_P, C.c_uint32, _P, _SZ, _P]),
@@ -530,6 +532,20 @@ def encode_points(field, xyz, h_out, stream=None):
     xyz = _dev(xyz, torch.float32, "xyz")
     _check(load().encode_points(field.handle, xyz.numel() // 3, _ptr(xyz), _ptr(h_out), _stream(stream)),
            "encode_points")
+
+
+def channel_mask_workspace_bytes(field, G: int) -> int:
+    out = C.c_size_t()
+    _check(load().channel_mask_workspace_bytes(field.handle, G, C.byref(out)), "channel_mask_workspace_bytes")
+    return out.value
+
+
+def select_channel_mask(field, G, cutoff, threshold, apply, frac_out, mask_out, ws, stream=None):
+    """FFT channel-mask selection in the library (include/nhcbct.h): frac_out float64
+    [L F] and mask_out float32 [L F] (or None) on the device; apply installs the mask."""
+    _check(load().field_select_channel_mask(field.handle, G, float(cutoff), float(threshold), int(bool(apply)),
+                                            _ptr(frac_out), _ptr(mask_out), _ptr(ws), ws.numel() * 4,
+                                            _stream(stream)), "field_select_channel_mask")
 
 
 def scatter_points(field, xyz, dh, stream=None):

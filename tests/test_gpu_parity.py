@@ -686,6 +686,41 @@ def test_fft_channel_mask_matches_oracle(lib):
     np.testing.assert_array_equal(masks[0], [1] * 14 + [0, 0])
 
 
+@pytest.mark.parametrize("precision,G", [(S.PREC_BF16, 33), (S.PREC_F32, 64)])
+def test_fft_channel_mask_selection_through_the_c_abi(lib, precision, G):
+    """field_select_channel_mask (Sec. 2.3) on the paper-scale field shape (L16 F2
+    16..2048, one LN; 2^16 entries per level): every channel's high-frequency
+    fraction within 1e-5 of the oracle's (tables rounded as the library stores
+    them), the mask equal wherever float32 feature rounding cannot flip the
+    decision, an odd grid (33^3) and the read-out grid (64^3), the same bits on a
+    second call, and the mask installed in the field only when asked."""
+    cfg = replace(S.WORKLOADS["paper_fp32"].field, precision=precision, log2_T=16)
+    flat = S.init_params(cfg, 17, table_scale=1.0).astype(np.float32)
+    tab = flat[: cfg.n_levels * cfg.T * 2].reshape(cfg.n_levels, cfg.T, 2)
+    tab[3] = 0.0                                      # a zero level: no variance, fraction 0
+    field = lib.Field(cfg, params=flat)
+    D = cfg.d_in
+    ws = lib.workspace(lib.channel_mask_workspace_bytes(field, G))
+    frac = torch.empty(D, dtype=torch.float64, device="cuda")
+    mask = torch.empty(D, device="cuda")
+    lib.select_channel_mask(field, G, 0.25, 0.85, False, frac, mask, ws)
+    torch.cuda.synchronize()
+    f1, m1 = _np(frac).copy(), _np(mask).copy()
+    assert np.all(_np(field.state)[16:16 + D] == 1.0)            # not installed
+    lib.select_channel_mask(field, G, 0.25, 0.85, True, frac, mask, ws)
+    torch.cuda.synchronize()
+    assert np.array_equal(_np(frac), f1) and np.array_equal(_np(mask), m1)
+    assert np.array_equal(_np(field.state)[16:16 + D], m1)        # installed
+    ref_mask, ref_frac = oracle.channel_mask(rounded_tables(flat, cfg, precision).astype(np.float64), cfg, G=G,
+                                             cutoff=0.25, threshold=0.85)
+    print(np.round(f1, 4))
+    np.testing.assert_allclose(f1, ref_frac, rtol=0, atol=1e-5)
+    assert f1[6] == 0.0 and f1[7] == 0.0
+    clear = np.abs(ref_frac - 0.85) > 1e-4
+    assert np.array_equal(m1[clear], ref_mask[clear].astype(np.float32))
+    assert 0 < m1.sum() < D                                      # both decisions occur
+
+
 # ------------------------------------------------------------------------------ stored record
 def test_library_matches_the_stored_oracle_step(lib):
     """The library against tests/golden/oracle_step.json (the oracle's record of one

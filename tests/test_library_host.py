@@ -284,3 +284,36 @@ def test_point_stage_and_export_validation_rejects_before_any_launch(nh):
     assert lib.render_backward(h, g, C.byref(nh.RayBatch(0, 64, fake, fake, 0)), fake, fake, need.value, None) == -1
     lib.field_destroy(h)
     lib.geometry_destroy(g)
+
+
+def test_channel_mask_selection_validation_rejects_before_any_launch(nh):
+    """Host checks of the FFT channel-mask selection (Sec. 2.3): grid size, cutoff,
+    threshold, null, misaligned and undersized buffers return their status codes
+    without touching the (fake) device addresses; the workspace is two complex FP64 planes of G^3 x L F values plus the
+    channel means."""
+    lib = nh.load()
+    f = S.WORKLOADS["paper_fp32"].field
+    h = _fake_field(nh, f)
+    fake = 1 << 40
+    need = C.c_size_t()
+    assert lib.channel_mask_workspace_bytes(h, 64, C.byref(need)) == 0
+    D = f.n_levels * f.n_feat
+    assert need.value >= 2 * 16 * 64 ** 3 * D + 8 * D and need.value % 256 == 0
+    assert lib.channel_mask_workspace_bytes(h, 1, C.byref(need)) == -1
+    assert lib.channel_mask_workspace_bytes(h, 129, C.byref(need)) == -1
+    assert lib.channel_mask_workspace_bytes(None, 64, C.byref(need)) == -1
+    assert lib.channel_mask_workspace_bytes(h, 64, C.byref(need)) == 0
+    sel = lib.field_select_channel_mask
+    assert sel(None, 64, 0.25, 0.85, 1, fake, fake, fake, need.value, None) == -1
+    assert sel(h, 64, 0.25, 0.85, 1, None, fake, fake, need.value, None) == -1
+    assert sel(h, 64, 0.25, 0.85, 1, fake, fake, None, need.value, None) == -1
+    assert sel(h, 1, 0.25, 0.85, 1, fake, fake, fake, need.value, None) == -1
+    assert sel(h, 200, 0.25, 0.85, 1, fake, fake, fake, need.value, None) == -1
+    assert sel(h, 64, -0.1, 0.85, 1, fake, fake, fake, need.value, None) == -1
+    assert sel(h, 64, float("nan"), 0.85, 1, fake, fake, fake, need.value, None) == -1
+    assert sel(h, 64, 0.25, float("inf"), 1, fake, fake, fake, need.value, None) == -1
+    assert sel(h, 64, 0.25, 0.85, 1, fake + 4, fake, fake, need.value, None) == -7
+    assert sel(h, 64, 0.25, 0.85, 1, fake, fake + 2, fake, need.value, None) == -7
+    assert sel(h, 64, 0.25, 0.85, 1, fake, fake, fake + 128, need.value, None) == -7
+    assert sel(h, 64, 0.25, 0.85, 1, fake, fake, fake, need.value - 1, None) == -3
+    lib.field_destroy(h)
