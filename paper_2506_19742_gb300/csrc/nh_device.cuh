@@ -180,8 +180,9 @@ __device__ __forceinline__ void red_add_f2(float* addr, float a, float b) {
 // lanes whose sample must not contribute pass zeros in dh. Consecutive lanes hold
 // consecutive samples of one ray, so lanes in the same cell of a level form one
 // contiguous run: where a level has such runs, each run is summed with a segmented
-// shuffle reduction (per corner and feature) and only its first lane issues the 8
-// vector atomics. Levels whose cells are all distinct scatter directly.
+// shuffle reduction (per corner and feature; as many doubling steps as the longest
+// run needs) and only its first lane issues the 8 vector atomics. Levels whose
+// cells are all distinct scatter directly.
 // dhrow: this lane's dL/dh in shared memory, element k at dhrow[k ^ lane] (2 L <= 32).
 template <int L>
 __device__ __forceinline__ void scatter_point(const FieldArgs& fa, const float x[3], const float* dhrow, int lane) {
@@ -212,8 +213,11 @@ __device__ __forceinline__ void scatter_point(const FieldArgs& fa, const float x
         if (heads != 0xffffffffu) {
             const uint32_t after = lane == 31 ? 0u : (heads & (0xffffffffu << (lane + 1)));
             const int seg_end = after ? (__ffs(after) - 2) : 31;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
+            // after the steps of offsets 1 .. off, every lane holds the sum over the
+            // next 2 off lanes of its run, so the longest run sets the step count
+            const int longest = (int)__reduce_max_sync(0xffffffffu, (unsigned)(seg_end - lane + 1));
+#pragma unroll 1
+            for (int off = 1; off < longest; off <<= 1) {
 #pragma unroll
                 for (int e = 0; e < 16; e++) {
                     const float t = __shfl_down_sync(0xffffffffu, v[e], off);

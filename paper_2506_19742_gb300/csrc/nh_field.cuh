@@ -124,11 +124,13 @@ __device__ __forceinline__ float field_mu(const FieldArgs& fa, const float* sp, 
 }  // namespace nh
 
 #include "nh_field_mma.cuh"
+#include "nh_field_tf32.cuh"
 
 namespace nh {
 
-// Low-precision tables run the MLP on tensor cores (warp-collective); float tables
-// run the per-thread FFMA MLP.
+// Low-precision tables run the MLP on 16-bit tensor cores (warp-collective). Float
+// tables run the per-thread FFMA MLP in the forward-only kernels and the TF32 x 3
+// tensor-core MLP (nh_field_tf32.cuh) in the training kernels.
 template <typename TT>
 constexpr bool kMmaPath = sizeof(TT) == 2;
 
@@ -255,12 +257,13 @@ static __global__ void __launch_bounds__(1024) k_ray_loss(const float* __restric
 }
 
 // ============================================================================ backward
-// Per-warp shared scratch (floats) of the FFMA path: stage [32][kW] (one layer
-// input, a row per sample) and dz [32][kW], both with XOR-swizzled float4 groups
-// (element j of row s at swz(s, j)), so that row writes, column reads and float4
-// reads of any group are conflict-free. Each sample's activations live in TMEM:
-// slot 0 holds hhat (or h without normalization), slot k (1 <= k < H) holds a_k,
-// the ReLU output of layer k-1; a_H waits in the stage tile.
+// Per-warp shared scratch (floats) of the FP32 path: an input tile [32][kW] (the
+// gather's level rows, then a layer's input rows or C fragments) and a dz tile
+// [32][kW]. The gather addresses the input tile with swz (XOR-swizzled float4
+// groups, element j of row s at swz(s, j)); the tensor-core MLP with tsw. Each
+// sample's activations live in TMEM: slot 0 holds hhat (or h without
+// normalization), slot k (1 <= k < H) holds a_k, the ReLU output of layer k-1; a_H
+// waits in the input tile.
 constexpr int kStage = 32 * kW;
 __host__ __device__ constexpr int warp_scratch_floats() { return kStage + 32 * kW; }
 constexpr int kBwdWarps = 8;
@@ -268,155 +271,6 @@ constexpr int kMaxTrainWarps = kMaxFusedChunks;
 
 __device__ __forceinline__ int swz(int s, int j) {   // column j of dz row s
     return s * kW + ((((j >> 2) ^ (s & 7)) << 2) | (j & 3));
-}
-
-template <int IN>
-__device__ __forceinline__ void stage_row(float* stage, int lane, const float (&v)[IN]) {
-#pragma unroll
-    for (int q = 0; q < IN / 4; q++)
-        *reinterpret_cast<float4*>(stage + swz(lane, 4 * q)) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2],
-                                                                           v[4 * q + 3]);
-}
-
-// Column permutation of the FFMA path's shared-memory accumulators of W_l: element
-// (j, i) lives at j IN + fswz(i, j, IN). A lane of warp_weight_grad owns a block of
-// JPL consecutive rows j and 4 consecutive columns i; the permutation puts the 32
-// lanes of each accumulation step on 32 banks (2-way for IN = 16).
-__host__ __device__ __forceinline__ int fswz(int i, int j, int IN) {
-    return IN == 32 ? (i ^ ((j >> 3) & 3)) : (i ^ ((j >> 2) & 3));
-}
-
-// Stores this lane's dz row, then the warp reduces dW[j][i] = sum_s dz[s][j] in[s][i]
-// (in[s][i] = ga_i * stage[s][i] + be_i; ga = gamma m, be = beta m for layer 0 with
-// normalization, else 1, 0) and db[j] = sum_s dz[s][j] (lane j) into the CTA
-// accumulators. Register blocking: lane (jb, ib) keeps the JPL x 4 block
-// j in [jb JPL, jb JPL + JPL), i in [4 ib, 4 ib + 4), reading per sample one float4
-// of the stage row and JPL / 4 float4 of the dz row (broadcast within a block row).
-template <int IN, bool AFFINE>
-__device__ __forceinline__ void warp_weight_grad(float* dzb, const float* stage, const float (&dz)[kW],
-                                                 const float* gamma, const float* beta, const float* mask,
-                                                 float* sgW, float* sgb, int lane) {
-    constexpr int IB = IN / 4;        // column groups of 4
-    constexpr int JPL = IB;           // rows per lane (8 for IN = 32, 4 for IN = 16)
-#pragma unroll
-    for (int q = 0; q < kW / 4; q++)
-        *reinterpret_cast<float4*>(dzb + swz(lane, 4 * q)) =
-            make_float4(dz[4 * q], dz[4 * q + 1], dz[4 * q + 2], dz[4 * q + 3]);
-    __syncwarp();
-    const int ib = lane % IB, jb = lane / IB;
-    float ga[4] = {1.f, 1.f, 1.f, 1.f}, be[4] = {0.f, 0.f, 0.f, 0.f};
-    if constexpr (AFFINE) {
-#pragma unroll
-        for (int t = 0; t < 4; t++) {
-            const int i = 4 * ib + t;
-            ga[t] = (gamma ? gamma[i] : 1.f) * mask[i];
-            be[t] = gamma ? beta[i] * mask[i] : 0.f;
-        }
-    }
-    // acc[p][t] holds rows (2p, 2p + 1) of column t: one paired FMA updates both,
-    // each element with the same single-rounded fma as a scalar FFMA
-    float2 acc[JPL / 2][4];
-#pragma unroll
-    for (int jp = 0; jp < JPL / 2; jp++)
-#pragma unroll
-        for (int t = 0; t < 4; t++) acc[jp][t] = make_float2(0.f, 0.f);
-#pragma unroll 1
-    for (int s = 0; s < 32; s++) {
-        const float4 a4 = *reinterpret_cast<const float4*>(stage + swz(s, 4 * ib));
-        float a[4] = {a4.x, a4.y, a4.z, a4.w};
-        if constexpr (AFFINE) {
-#pragma unroll
-            for (int t = 0; t < 4; t++) a[t] = fmaf(ga[t], a[t], be[t]);
-        }
-        float2 aa[4];
-#pragma unroll
-        for (int t = 0; t < 4; t++) aa[t] = make_float2(a[t], a[t]);
-#pragma unroll
-        for (int q = 0; q < JPL / 4; q++) {
-            const float4 d = *reinterpret_cast<const float4*>(dzb + swz(s, 4 * (jb * (JPL / 4) + q)));
-            const float2 d01 = make_float2(d.x, d.y), d23 = make_float2(d.z, d.w);
-#pragma unroll
-            for (int t = 0; t < 4; t++) {
-                acc[2 * q][t] = __ffma2_rn(d01, aa[t], acc[2 * q][t]);
-                acc[2 * q + 1][t] = __ffma2_rn(d23, aa[t], acc[2 * q + 1][t]);
-            }
-        }
-    }
-#pragma unroll
-    for (int jj = 0; jj < JPL; jj++)
-#pragma unroll
-        for (int t = 0; t < 4; t++) {
-            const int j = jb * JPL + jj, i = 4 * ib + t;
-            atomicAdd(sgW + j * IN + fswz(i, j, IN), (jj & 1) ? acc[jj / 2][t].y : acc[jj / 2][t].x);
-        }
-    float bsum = 0.f;
-#pragma unroll 8
-    for (int s = 0; s < 32; s++) bsum += dzb[swz(s, lane)];
-    atomicAdd(sgb + lane, bsum);
-    __syncwarp();
-}
-
-// Layer products of the FFMA path with the output loop rolled four outputs at a time
-// (one copy of the code per layer shape). linear_fwd_rolled: out[j] = b[j] +
-// sum_i W[j][i] in[i], the four outputs of a step parked in the lane's row of `row`
-// (swizzled float4 groups) and read back at the end. linear_bwd_data_rolled:
-// din[i] = sum_j W[j][i] dz[j] with dz read from the lane's row of `dzrow`
-// (swizzled float4 groups, as warp_weight_grad leaves it).
-template <int IN>
-__device__ __forceinline__ void linear_fwd_rolled(const float* __restrict__ sW, const float* __restrict__ sb,
-                                                  const float (&in)[IN], float (&out)[kW], float* row, int lane) {
-#pragma unroll 1
-    for (int jq = 0; jq < kW / 4; jq++) {
-        float acc[4];
-#pragma unroll
-        for (int e = 0; e < 4; e++) {
-            const int j = 4 * jq + e;
-            float2 a = make_float2(sb[j], 0.f);        // (bias + even terms, odd terms), as linear_fwd
-#pragma unroll
-            for (int i = 0; i < IN; i += 4) {
-                const float4 w = *reinterpret_cast<const float4*>(sW + j * IN + i);
-                a = __ffma2_rn(make_float2(w.x, w.y), make_float2(in[i], in[i + 1]), a);
-                a = __ffma2_rn(make_float2(w.z, w.w), make_float2(in[i + 2], in[i + 3]), a);
-            }
-            acc[e] = a.x + a.y;
-        }
-        *reinterpret_cast<float4*>(row + swz(lane, 4 * jq)) = make_float4(acc[0], acc[1], acc[2], acc[3]);
-    }
-#pragma unroll
-    for (int q = 0; q < kW / 4; q++) {
-        const float4 v = *reinterpret_cast<const float4*>(row + swz(lane, 4 * q));
-        out[4 * q] = v.x;
-        out[4 * q + 1] = v.y;
-        out[4 * q + 2] = v.z;
-        out[4 * q + 3] = v.w;
-    }
-}
-
-template <int IN>
-__device__ __forceinline__ void linear_bwd_data_rolled(const float* __restrict__ sW, const float* dzrow, int lane,
-                                                       float (&din)[IN]) {
-#pragma unroll
-    for (int i = 0; i < IN; i++) din[i] = 0.f;
-#pragma unroll 1
-    for (int jq = 0; jq < kW / 4; jq++) {
-        const float4 d4 = *reinterpret_cast<const float4*>(dzrow + swz(lane, 4 * jq));
-        const float d[4] = {d4.x, d4.y, d4.z, d4.w};
-#pragma unroll
-        for (int e = 0; e < 4; e++) {
-            const int j = 4 * jq + e;
-            const float2 dd = make_float2(d[e], d[e]);
-#pragma unroll
-            for (int i = 0; i < IN; i += 4) {
-                const float4 w = *reinterpret_cast<const float4*>(sW + j * IN + i);
-                const float2 lo = __ffma2_rn(make_float2(w.x, w.y), dd, make_float2(din[i], din[i + 1]));
-                const float2 hi = __ffma2_rn(make_float2(w.z, w.w), dd, make_float2(din[i + 2], din[i + 3]));
-                din[i] = lo.x;
-                din[i + 1] = lo.y;
-                din[i + 2] = hi.x;
-                din[i + 3] = hi.y;
-            }
-        }
-    }
 }
 
 // Normalized Hash Encoder backward and the hash scatter of one sample per lane.
@@ -515,137 +369,159 @@ __device__ __forceinline__ void encode_point_rolled(const FieldArgs& fa, const v
     }
 }
 
-// State of one training sample carried from the forward half to the backward half:
-// FFMA path. Everything else waits in tensor memory (hhat, a_1 .. a_{H-1}) or, for
-// a_H, in the warp's stage tile of shared memory.
+// State of one training sample carried from the forward half to the backward half
+// (FP32 path). Everything else waits in tensor memory (slot 0: hhat, the lane's
+// row; slot k, 1 <= k < H: a_k as the lane's 32 C-fragment values) or, for a_H, in
+// the warp's input tile (C-fragment layout).
 template <int D, int G>
-struct FfmaCarry {
+struct F32Carry {
     float rstd[G];     // normalization groups: 1 (one LayerNorm / none) or L (per level)
     float mu;
 };
 
-// Forward of one sample per lane with activations kept in TMEM (slot 0: hhat, slot
-// k: a_k); a_H goes to row `lane` of the stage tile (wbuf), where the backward's
-// output layer reads it. All 32 lanes must call it together.
+template <int NT>
+__device__ __forceinline__ void relu_frag(const float (&z)[2][NT][4], float (&a)[2][NT][4]) {
+#pragma unroll
+    for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+        for (int nt = 0; nt < NT; nt++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) a[mt][nt][c] = fmaxf(z[mt][nt][c], 0.f);
+}
+__device__ __forceinline__ void frag_tmem_st(uint32_t taddr, const float (&a)[2][4][4]) {
+    float v[32];
+#pragma unroll
+    for (int i = 0; i < 32; i++) v[i] = a[i >> 4][(i >> 2) & 3][i & 3];
+    tmem_st(taddr, v);
+}
+__device__ __forceinline__ void frag_tmem_ld(uint32_t taddr, float (&a)[2][4][4]) {
+    float v[32];
+    tmem_ld(taddr, v);
+#pragma unroll
+    for (int i = 0; i < 32; i++) a[i >> 4][(i >> 2) & 3][i & 3] = v[i];
+}
+
+// Layer-0 input y = (gamma hhat + beta) m of this lane's sample (hhat = h without
+// normalization).
+template <int D>
+__device__ __forceinline__ void affine_row(const FieldArgs& fa, const float* sp, const float* smask,
+                                           const float (&hhat)[D], float (&y)[D]) {
+    const bool affine = fa.norm != NH_NORM_NONE;
+#pragma unroll
+    for (int k = 0; k < D; k++) y[k] = (affine ? fmaf(sp[k], hhat[k], sp[D + k]) : hhat[k]) * smask[k];
+}
+
+// Forward of one sample per lane, the MLP on tensor cores (nh_field_tf32.cuh). All 32
+// lanes must call it together. Warp scratch: the input tile (wbuf) and the dz tile
+// (wbuf + 32 x 32), the latter also the output layer's row buffer.
 template <int D, int G, typename TT>
-__device__ __forceinline__ void ffma_forward(const FieldArgs& fa, const float* sp, const float* smask,
-                                             float* wbuf, uint32_t tslot0, const float x[3], int lane,
-                                             FfmaCarry<D, G>& s) {
+__device__ __forceinline__ void f32_forward(const FieldArgs& fa, const float* sp, const float* smask, float* wbuf,
+                                            uint32_t tslot0, const float x[3], int lane, F32Carry<D, G>& s) {
     constexpr int L = D / 2;
     const DenseLayout lay{D, fa.H};
     const int H = fa.H;
-    // With D = kW layer 0 runs in the hidden layers' loop: one copy of the unrolled
-    // layer code instead of two keeps more of the kernel in the instruction cache.
-    constexpr int k0 = (D == kW) ? 0 : 1;
-    float a[kW];
+    float* act = wbuf;
+    float* dzt = wbuf + kStage;
+    float z[2][4][4];
     {
         float h[D], hhat[D], y[D];
-        __syncwarp();   // the previous sample's readers of the stage tile are done
-        encode_point_rolled<L, TT>(fa, table_base<TT>(fa), x, wbuf, lane, h);
+        __syncwarp();   // the previous sample's readers of the tiles are done
+        encode_point_rolled<L, TT>(fa, table_base<TT>(fa), x, act, lane, h);
         nhe_forward<D, G>(fa, sp, smask, h, hhat, s.rstd, y);
         tmem_st(tslot0, hhat);
-        if constexpr (D == kW) {
-#pragma unroll
-            for (int j = 0; j < kW; j++) a[j] = y[j];
-        } else {
-            float z[kW];
-            linear_fwd<D, kW>(sp + lay.W(0), sp + lay.b(0), y, z);
-#pragma unroll
-            for (int j = 0; j < kW; j++) a[j] = fmaxf(z[j], 0.f);
-        }
+        __syncwarp();   // the gather's reads of the tile are done
+        row_to_tile<D>(act, lane, y);
+        __syncwarp();
+        tf32_layer_tile<D / 8>(act, sp + lay.W(0), sp + lay.b(0), lane, z);
     }
+    float a[2][4][4];
 #pragma unroll 1
-    for (int k = k0; k < H; k++) {
-        if (k > 0) tmem_st(tslot0 + 32 * k, a);
-        float z[kW];
-        linear_fwd_rolled<kW>(sp + lay.W(k), sp + lay.b(k), a, z, wbuf, lane);
-#pragma unroll
-        for (int j = 0; j < kW; j++) a[j] = fmaxf(z[j], 0.f);
+    for (int k = 1; k < H; k++) {
+        relu_frag<4>(z, a);
+        frag_tmem_st(tslot0 + 32 * k, a);
+        tf32_layer_frag(a, sp + lay.W(k), sp + lay.b(k), lane, z);
     }
-    const float* wo = sp + lay.W(H);
-    float zo = sp[lay.b(H)];
-#pragma unroll
-    for (int j = 0; j < kW; j++) zo = fmaf(wo[j], a[j], zo);
-    s.mu = 1.f / (1.f + expf(-zo));
-    __syncwarp();   // the previous sample's readers of the stage tile are done
-    stage_row<kW>(wbuf, lane, a);
+    relu_frag<4>(z, a);
+    s.mu = tf32_out_forward(sp + lay.W(H), sp[lay.b(H)], a, dzt, lane);
+    __syncwarp();   // every lane's layer-0 reads of the input tile are done
+    frag_to_tile<4>(act, lane, a);   // a_H waits here for the backward
 }
 
 // Backward of one sample per lane given dL/dmu (already multiplied by the loss
 // scale; 0 for lanes without a sample). All 32 lanes must call it together.
 template <int D, int G, typename TT>
-__device__ __forceinline__ void ffma_backward(const FieldArgs& fa, const float* sp, const float* smask, float* sg,
-                                              float* wbuf, uint32_t tslot0, const float x[3], bool active, int lane,
-                                              const FfmaCarry<D, G>& s, float dmu) {
+__device__ __forceinline__ void f32_backward(const FieldArgs& fa, const float* sp, const float* smask, float* sg,
+                                             float* wbuf, uint32_t tslot0, const float x[3], bool active, int lane,
+                                             const F32Carry<D, G>& s, float dmu) {
     const DenseLayout lay{D, fa.H};
     const int H = fa.H;
-    float* stage = wbuf;
-    float* dzb = wbuf + kStage;
-    const float mu = s.mu;
-    const float dzo = dmu * mu * (1.f - mu);
-    const float* wo = sp + lay.W(H);
-
-    // output layer: dW_H[0][i] = sum_s dzo[s] a_H[s][i], db_H = sum_s dzo[s]; the
-    // stage tile holds a_H from the forward
-    dzb[lane] = dzo;
-    float dz[kW];
-#pragma unroll
-    for (int q = 0; q < kW / 4; q++) {
-        const float4 a4 = *reinterpret_cast<const float4*>(stage + swz(lane, 4 * q));
-        dz[4 * q] = a4.x > 0.f ? wo[4 * q] * dzo : 0.f;
-        dz[4 * q + 1] = a4.y > 0.f ? wo[4 * q + 1] * dzo : 0.f;
-        dz[4 * q + 2] = a4.z > 0.f ? wo[4 * q + 2] * dzo : 0.f;
-        dz[4 * q + 3] = a4.w > 0.f ? wo[4 * q + 3] * dzo : 0.f;
-    }
-    __syncwarp();
+    float* act = wbuf;
+    float* dzt = wbuf + kStage;
+    const float dzo = dmu * s.mu * (1.f - s.mu);
+    float dz[2][4][4];
     {
-        float acc = 0.f;
-#pragma unroll 8
-        for (int t = 0; t < 32; t++) acc = fmaf(dzb[t], stage[swz(t, lane)], acc);
-        atomicAdd(sg + lay.W(H) + lane, acc);
-        const float bs = warp_sum(dzo);
-        if (lane == 0) atomicAdd(sg + lay.b(H), bs);
+        float a[2][4][4];
+        __syncwarp();
+        tile_to_frag<4>(act, lane, a);   // a_H
+        out_layer_backward_mma<4>(lay, sp, sg, dzt, lane, dzo, a, dz);
     }
-    __syncwarp();
-
     // hidden layers k = H-1 .. 1: input a_k from TMEM
 #pragma unroll 1
     for (int k = H - 1; k >= 1; k--) {
-        uint32_t pos = 0u;
+        add_colsum<4>(dz, sg + lay.b(k), lane);
         {
-            float ak[kW];
-            tmem_ld(tslot0 + 32 * k, ak);
-#pragma unroll
-            for (int i = 0; i < kW; i++) pos |= (ak[i] > 0.f ? 1u : 0u) << i;
-            stage_row<kW>(stage, lane, ak);
+            float a[2][4][4];
+            frag_tmem_ld(tslot0 + 32 * k, a);
+            __syncwarp();   // the previous readers of both tiles are done
+            frag_to_tile<4>(dzt, lane, dz);
+            frag_to_tile<4>(act, lane, a);
+            __syncwarp();
         }
-        warp_weight_grad<kW, false>(dzb, stage, dz, nullptr, nullptr, nullptr, sg + lay.W(k), sg + lay.b(k), lane);
-        float din[kW];
-        linear_bwd_data_rolled<kW>(sp + lay.W(k), dzb, lane, din);
+        tf32_wgrad<kW>(dzt, act, sg + lay.W(k), lane);
+        float din[2][4][4];
+        tf32_dgrad<4>(dz, sp + lay.W(k), lane, din);
+        float a[2][4][4];
+        frag_tmem_ld(tslot0 + 32 * k, a);
 #pragma unroll
-        for (int i = 0; i < kW; i++) dz[i] = ((pos >> i) & 1u) ? din[i] : 0.f;
+        for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+            for (int nt = 0; nt < 4; nt++)
+#pragma unroll
+                for (int c = 0; c < 4; c++) dz[mt][nt][c] = a[mt][nt][c] > 0.f ? din[mt][nt][c] : 0.f;
     }
-
     // layer 0: input y = (gamma hhat + beta) m
+    add_colsum<4>(dz, sg + lay.b(0), lane);
     float hhat[D];
     tmem_ld(tslot0, hhat);
-    stage_row<D>(stage, lane, hhat);
-    const bool affine = fa.norm != NH_NORM_NONE;
-    warp_weight_grad<D, true>(dzb, stage, dz, affine ? sp : nullptr, affine ? sp + D : nullptr, smask,
-                              sg + lay.W(0), sg + lay.b(0), lane);
+    {
+        float y[D];
+        affine_row<D>(fa, sp, smask, hhat, y);
+        __syncwarp();
+        frag_to_tile<4>(dzt, lane, dz);
+        row_to_tile<D>(act, lane, y);
+        __syncwarp();
+    }
+    tf32_wgrad<D>(dzt, act, sg + lay.W(0), lane);
     float dh[D];
-    linear_bwd_data_rolled<D>(sp + lay.W(0), dzb, lane, dh);   // dh <- dL/dy
-    nhe_backward_scatter<D, G>(fa, sp, smask, sg, dzb, hhat, s.rstd, dh, x, active, lane);
+    {
+        float din[2][D / 8][4];
+        tf32_dgrad<D / 8>(dz, sp + lay.W(0), lane, din);
+        __syncwarp();   // the weight gradient's reads of the input tile are done
+        frag_to_tile<D / 8>(act, lane, din);
+        __syncwarp();
+        tile_to_row<D>(act, lane, dh);   // dh <- dL/dy
+    }
+    nhe_backward_scatter<D, G>(fa, sp, smask, sg, dzt, hhat, s.rstd, dh, x, active, lane);
 }
 
 // Forward then backward of one sample per lane; dmu_of(mu) gives dL/dmu.
 template <int D, int G, typename TT, class DmuFn>
-__device__ __forceinline__ float sample_fwd_bwd(const FieldArgs& fa, const float* sp, const float* smask,
-                                                float* sg, float* wbuf, uint32_t tslot0, const float x[3],
-                                                bool active, int lane, DmuFn dmu_of) {
-    FfmaCarry<D, G> s;
-    ffma_forward<D, G, TT>(fa, sp, smask, wbuf, tslot0, x, lane, s);
-    ffma_backward<D, G, TT>(fa, sp, smask, sg, wbuf, tslot0, x, active, lane, s, active ? dmu_of(s.mu) : 0.f);
+__device__ __forceinline__ float sample_fwd_bwd(const FieldArgs& fa, const float* sp, const float* smask, float* sg,
+                                                float* wbuf, uint32_t tslot0, const float x[3], bool active,
+                                                int lane, DmuFn dmu_of) {
+    F32Carry<D, G> s;
+    f32_forward<D, G, TT>(fa, sp, smask, wbuf, tslot0, x, lane, s);
+    f32_backward<D, G, TT>(fa, sp, smask, sg, wbuf, tslot0, x, active, lane, s, active ? dmu_of(s.mu) : 0.f);
     return s.mu;
 }
 
@@ -725,9 +601,9 @@ __device__ __forceinline__ float sample_fwd_bwd_mma(const FieldArgs& fa, const f
     return s.mu;
 }
 
-// TMEM columns of one thread: FFMA path 32 H (hhat, a_1 .. a_{H-1}); tensor-core
-// path 64 + 16 H (hhat, the A fragments of every layer input, the last hidden
-// layer's pre-activations).
+// TMEM columns of one thread: FP32 path 32 H (hhat, a_1 .. a_{H-1}); 16-bit path
+// 64 + 16 H (hhat, the A fragments of every layer input, the last hidden layer's
+// pre-activations).
 __host__ __device__ inline int bwd_cols_per_thread(int precision, int H) {
     return precision == NH_PREC_F32 ? 32 * H : mma_tmem_cols_per_thread(H) + 32;
 }
@@ -737,13 +613,14 @@ static uint32_t bwd_tmem_cols(const FieldArgs& fa, int nwarps = kBwdWarps) {
     while (c < need) c <<= 1;
     return c;
 }
-// Shared memory of the backward kernels (bytes): float dense params, mask, gradient
-// accumulators, 16-bit weights (tensor-core path) and 8 warps of scratch. Registers
+// Shared memory of the backward kernels (bytes): float dense params (on the FP32
+// path with W_l^T tiles in place of W_l, l < H), mask, gradient accumulators, 16-bit
+// weights (16-bit path) and 8 warps of scratch. Registers
 // cap residency at two CTAs per SM; when one CTA takes all 512 TMEM columns the
 // request is padded so that only one CTA fits, and no tcgen05.alloc waits on a
 // resident CTA.
-// Per-warp scratch floats of the training kernels: the FFMA path's stage + dz tiles,
-// or the tensor-core path's two 16-bit tiles and row buffer.
+// Per-warp scratch floats of the training kernels: the FP32 path's input + dz tiles,
+// or the 16-bit path's two 16-bit tiles and row buffer.
 __host__ __device__ inline int bwd_warp_floats(int precision) {
     return precision == NH_PREC_F32 ? warp_scratch_floats() : kMmaWarpFloats;
 }
@@ -759,7 +636,7 @@ static size_t bwd_smem_bytes(const FieldArgs& fa, int nwarps = kBwdWarps) {
 // CTA prologue / epilogue shared by the training kernels.
 struct BwdCta {
     float *sp, *smask, *sg, *wbuf;
-    const uint16_t* sw;
+    const uint16_t* sw;   // 16-bit path: W and W^T per layer
     uint32_t tbase, tslot0;
 };
 
@@ -778,10 +655,11 @@ __device__ __forceinline__ BwdCta bwd_begin(const FieldArgs& fa, float* smem, ui
     if (warp == 0) tmem_alloc(s_tmem, tcols);
     load_dense(fa, c.sp, c.smask);
     for (int k = threadIdx.x; k < ndp; k += blockDim.x) c.sg[k] = 0.f;
-    if constexpr (kMmaPath<TT>) {
-        __syncthreads();
+    __syncthreads();
+    if constexpr (kMmaPath<TT>)
         stage_weights16<TT>(c.sp, DenseLayout{fa.D, fa.H}, fa.D, sw);
-    }
+    else
+        stage_wt_tf32(fa.params + fa.n_table, DenseLayout{fa.D, fa.H}, fa.D, c.sp);
     tmem_fence_before_sync();
     __syncthreads();
     tmem_fence_after_sync();
@@ -790,7 +668,7 @@ __device__ __forceinline__ BwdCta bwd_begin(const FieldArgs& fa, float* smem, ui
     return c;
 }
 
-// One training sample per lane through the FFMA or the tensor-core MLP.
+// One training sample per lane through the FP32 (TF32 x 3) or the 16-bit tensor-core MLP.
 template <int D, int G, typename TT, class DmuFn>
 __device__ __forceinline__ float train_sample(const FieldArgs& fa, const BwdCta& c, const float x[3], bool active,
                                               int lane, DmuFn dmu_of) {
@@ -816,7 +694,7 @@ __device__ __forceinline__ void bwd_end(const FieldArgs& fa, const BwdCta& c, ui
             const int IN = l == 0 ? fa.D : kW, o = k - lay.W(l);
             if (o >= 0 && o < kW * IN) {
                 const int j = o / IN, i = o - j * IN;
-                p = lay.W(l) + j * IN + (fa.precision == NH_PREC_F32 ? fswz(i, j, IN) : wswz(i, j, IN));
+                p = lay.W(l) + j * IN + wswz(i, j, IN);
             }
         }
         const float v = c.sg[p];
@@ -860,7 +738,7 @@ k_ray_backward(FieldArgs fa, ViewArgs va, const int32_t* __restrict__ pix, int R
 // order per CTA; k_train_loss adds the CTA partials in a fixed order.
 template <int D, int G, typename TT>
 struct TrainCarry {
-    using type = FfmaCarry<D, G>;
+    using type = F32Carry<D, G>;
 };
 
 template <int D, int G>
@@ -911,7 +789,7 @@ k_ray_train(FieldArgs fa, ViewArgs va, const int32_t* __restrict__ pix, const fl
             if constexpr (kMmaPath<TT>)
                 mma_forward<D, G, TT>(fa, cta.sp, cta.sw, cta.smask, cta.wbuf, cta.tslot0, x, lane, st);
             else
-                ffma_forward<D, G, TT>(fa, cta.sp, cta.smask, cta.wbuf, cta.tslot0, x, lane, st);
+                f32_forward<D, G, TT>(fa, cta.sp, cta.smask, cta.wbuf, cta.tslot0, x, lane, st);
         }
         const float part = warp_sum(active ? st.mu : 0.f) * (work ? g.delta : 0.f);
         if (lane == 0) s_part[warp] = part;
@@ -943,7 +821,8 @@ k_ray_train(FieldArgs fa, ViewArgs va, const int32_t* __restrict__ pix, const fl
                 mma_backward<D, G, TT>(fa, cta.sp, cta.sw, cta.smask, cta.sg, cta.wbuf, cta.tslot0, x, active, lane, st,
                                     dmu);
             else
-                ffma_backward<D, G, TT>(fa, cta.sp, cta.smask, cta.sg, cta.wbuf, cta.tslot0, x, active, lane, st, dmu);
+                f32_backward<D, G, TT>(fa, cta.sp, cta.smask, cta.sg, cta.wbuf, cta.tslot0, x, active, lane,
+                                        st, dmu);
         }
     }
     bwd_end(fa, cta, tcols);
