@@ -464,7 +464,8 @@ def l2_roofline(nh, torch, geom, fields, batch, N, dev):
     n = R * N
     out = {"l2_read_gbs": round(l2_gbs, 1), "points": n,
            "method": "probe_l2_read of a 48 MB buffer x10 sweeps; probe_random_gather / probe_random_red "
-                     "on tables of the stage's size; encode_points / scatter_points at one batch's samples"}
+                     "(float2) / probe_random_red16 (bf16x2) on tables of the stage's size; encode_points / "
+                     "scatter_points at one batch's samples"}
     for name, fld in fields.items():
         cfg = fld.cfg
         L, F = cfg.n_levels, cfg.n_feat
@@ -495,10 +496,17 @@ def l2_roofline(nh, torch, geom, fields, batch, N, dev):
         def rprobe():
             done[0] = nh.probe_random_red(gtab, corners)
         t_pr = event_ms(torch, rprobe)
+        n16 = [0]
+        gtab16 = fld.grads[: n_ent]                          # n_ent 4-byte entries
+
+        def rprobe16():
+            n16[0] = nh.probe_random_red16(gtab16, S.PREC_BF16, corners)
+        t_pr16 = event_ms(torch, rprobe16)
         fld.grads.zero_()
         scatter = {"ms": round(t_s, 4), "corner_atomics": corners,
                    "algorithmic_gbs": round(corners * F * 4 / (t_s / 1e3) / 1e9, 1),
-                   "probe_random_atomics_per_s": done[0] / (t_pr / 1e3)}
+                   "probe_random_atomics_per_s": done[0] / (t_pr / 1e3),
+                   "probe_random_bf16x2_atomics_per_s": n16[0] / (t_pr16 / 1e3)}
         scatter["frac_l2_algorithmic"] = round(scatter["algorithmic_gbs"] / l2_gbs, 4)
         scatter["frac_random_probe"] = round((corners / (t_s / 1e3)) / scatter["probe_random_atomics_per_s"], 4)
         out[name] = {"table_mb": round(tbytes / 1e6, 1), "gather": gather, "scatter": scatter}

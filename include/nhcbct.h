@@ -360,11 +360,16 @@ nh_status scatter_points(nh_field* f, int32_t n, const float* xyz_dev, const flo
  *   launch's granularity).
  * probe_random_red: uniformly random red.global.add.v2.f32 of 1e-30 into the
  *   float2 entries of table_dev (n_entries a power of two, 8-byte aligned); the
- *   table's values change. *n_done as above. */
+ *   table's values change. *n_done as above.
+ * probe_random_red16: the same with packed 16-bit reductions (fmt NH_PREC_BF16:
+ *   bf16x2, NH_PREC_F16: f16x2) into 4-byte entries (4-byte aligned): the scatter
+ *   that 16-bit gradient tables would issue. */
 nh_status probe_l2_read(const void* buf_dev, uint64_t bytes, int32_t reps, float* sink_dev, void* stream);
 nh_status probe_random_gather(const void* table_dev, uint64_t n_entries, int32_t entry_bytes, int64_t n_loads,
                               float* sink_dev, int64_t* n_done, void* stream);
 nh_status probe_random_red(float* table_dev, uint64_t n_entries, int64_t n_ops, int64_t* n_done, void* stream);
+nh_status probe_random_red16(void* table_dev, uint64_t n_entries, int32_t fmt, int64_t n_ops, int64_t* n_done,
+                             void* stream);
 
 #ifdef __cplusplus
 }

@@ -704,6 +704,16 @@ extern "C" nh_status probe_random_red(float* table, uint64_t n_entries, int64_t 
     return NH_OK;
 }
 
+extern "C" nh_status probe_random_red16(void* table, uint64_t n_entries, int32_t fmt, int64_t n_ops,
+                                        int64_t* n_done, void* stream) {
+    if (!table || !n_done) return fail(NH_ERR_INVALID_ARG, "probe_random_red16: null argument");
+    if (!pow2(n_entries) || n_entries > (uint64_t(1) << 32) || n_ops < 0 || (fmt != NH_PREC_BF16 && fmt != NH_PREC_F16))
+        return fail(NH_ERR_INVALID_ARG, "probe_random_red16: n_entries a power of two <= 2^32, fmt BF16 or F16");
+    if (!aligned(table, 4)) return fail(NH_ERR_ALIGNMENT, "probe_random_red16: table must be 4-byte aligned");
+    NH_CUDA(launch_probe_random_red16(table, n_entries, fmt, n_ops, n_done, S(stream)), "probe_random_red16");
+    return NH_OK;
+}
+
 extern "C" nh_status volume_mse(const float* a, const float* b, int64_t n, double* out_dev, void* ws,
                                 size_t ws_bytes, void* stream) {
     NH_RANGE("volume_mse");

@@ -241,38 +241,53 @@ __device__ __forceinline__ void tf32_dgrad(const float (&dz)[2][4][4], const flo
 // Weight gradient dW[j][i] = sum_s dz[s][j] act[s][i] of the warp's 32 samples,
 // added to the CTA accumulator gW (element (j, i) at j IN + wswz(i, j, IN)).
 // M = j (two 16-row halves), N = i (IN / 8 n-tiles), K = s (four k-steps); A and B
-// come from the dz and input tiles.
+// come from the dz and input tiles. Each k-step splits its B values once for both
+// halves of j.
 template <int IN>
 __device__ __forceinline__ void tf32_wgrad(const float* dzt, const float* act, float* gW, int lane) {
     constexpr int NT = IN / 8;
     const int g = lane >> 2, t = lane & 3;
-#pragma unroll 1
-    for (int mj = 0; mj < 2; mj++) {
-        float dw[NT][4];
+    float dw[2][NT][4];
+#pragma unroll
+    for (int mj = 0; mj < 2; mj++)
 #pragma unroll
         for (int nt = 0; nt < NT; nt++)
 #pragma unroll
-            for (int c = 0; c < 4; c++) dw[nt][c] = 0.f;
+            for (int c = 0; c < 4; c++) dw[mj][nt][c] = 0.f;
 #pragma unroll
-        for (int ks = 0; ks < 4; ks++) {
-            const int s0 = 8 * ks + t, s1 = s0 + 4, j0 = 16 * mj + g;
+    for (int ks = 0; ks < 4; ks++) {
+        const int s0 = 8 * ks + t, s1 = s0 + 4;
+        uint32_t bh[NT][2], bl[NT][2];
+#pragma unroll
+        for (int nt = 0; nt < NT; nt++) {
+            split_tf32(act[tsw(s0, 8 * nt + g)], bh[nt][0], bl[nt][0]);
+            split_tf32(act[tsw(s1, 8 * nt + g)], bh[nt][1], bl[nt][1]);
+        }
+#pragma unroll
+        for (int mj = 0; mj < 2; mj++) {
+            const int j0 = 16 * mj + g;
             uint32_t ah[4], al[4];
             split_tf32(dzt[tsw(s0, j0)], ah[0], al[0]);
             split_tf32(dzt[tsw(s0, j0 + 8)], ah[1], al[1]);
             split_tf32(dzt[tsw(s1, j0)], ah[2], al[2]);
             split_tf32(dzt[tsw(s1, j0 + 8)], ah[3], al[3]);
 #pragma unroll
-            for (int nt = 0; nt < NT; nt++)
-                mma3(dw[nt], ah, al, act[tsw(s0, 8 * nt + g)], act[tsw(s1, 8 * nt + g)]);
+            for (int nt = 0; nt < NT; nt++) {
+                mma_tf32(dw[mj][nt], al, bh[nt][0], bh[nt][1]);
+                mma_tf32(dw[mj][nt], ah, bl[nt][0], bl[nt][1]);
+                mma_tf32(dw[mj][nt], ah, bh[nt][0], bh[nt][1]);
+            }
         }
+    }
+#pragma unroll
+    for (int mj = 0; mj < 2; mj++)
 #pragma unroll
         for (int nt = 0; nt < NT; nt++)
 #pragma unroll
             for (int c = 0; c < 4; c++) {
                 const int j = 16 * mj + g + 8 * (c >> 1), i = 8 * nt + 2 * t + (c & 1);
-                atomicAdd(gW + j * IN + wswz(i, j, IN), dw[nt][c]);
+                atomicAdd(gW + j * IN + wswz(i, j, IN), dw[mj][nt][c]);
             }
-    }
 }
 
 // mu = sigmoid(b_o + sum_j w_o[j] a[s][j]) of the warp's samples from the last

@@ -98,6 +98,8 @@ cudaError_t launch_probe_random_gather(const void* table, size_t n_entries, int 
                                        float* sink, int64_t* n_done, cudaStream_t st);
 cudaError_t launch_probe_random_red(float* table, size_t n_entries, int64_t n_ops, int64_t* n_done,
                                     cudaStream_t st);
+cudaError_t launch_probe_random_red16(void* table, size_t n_entries, int fmt, int64_t n_ops, int64_t* n_done,
+                                      cudaStream_t st);
 size_t      mse_workspace_bytes();
 // sms, occupancy (CTAs/SM by registers and shared memory), CTAs/SM by TMEM, grid,
 // TMEM columns per CTA, dynamic shared memory bytes of the last training launch

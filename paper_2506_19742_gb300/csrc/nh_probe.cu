@@ -8,9 +8,14 @@
 //  k_random_gather  independent random 4- or 8-byte loads from a table (the hashed
 //                   levels' corner loads), eight in flight per thread
 //  k_random_red     random red.global.add.v2.f32 into a float2 table (the scatter)
+//  k_random_red16   random packed 16-bit reductions (bf16x2 or f16x2, 4 bytes) into a
+//                   table of 4-byte entries: the scatter a 16-bit gradient table
+//                   would issue
 //
 // Random indices come from a multiply-xorshift integer mix (the lowbias32 constants
 // published by C. Wellons) of a per-thread counter.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "nh_internal.h"
@@ -90,6 +95,22 @@ __global__ void __launch_bounds__(256) k_random_red(float* __restrict__ table, u
     }
 }
 
+template <int FMT>
+__global__ void __launch_bounds__(256) k_random_red16(void* __restrict__ table, uint32_t mask, int64_t per_thread) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t seed = mix32(t * 2u + 1u);
+    for (int64_t j = 0; j < per_thread; j += 8) {
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const uint32_t idx = mix32(seed ^ (uint32_t)(j + k) * 0x9e3779b9u) & mask;
+            if constexpr (FMT == 1)
+                atomicAdd(reinterpret_cast<__nv_bfloat162*>(table) + idx, __floats2bfloat162_rn(1e-30f, 1e-30f));
+            else
+                atomicAdd(reinterpret_cast<__half2*>(table) + idx, __floats2half2_rn(1e-7f, 1e-7f));
+        }
+    }
+}
+
 static int probe_blocks() {
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
@@ -131,6 +152,20 @@ cudaError_t launch_probe_random_red(float* table, size_t n_entries, int64_t n_op
     const int64_t pt = per_thread_of(n_ops, blocks * 256);
     *n_done = pt * blocks * 256;
     k_random_red<<<blocks, 256, 0, st>>>(table, (uint32_t)(n_entries - 1), pt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_probe_random_red16(void* table, size_t n_entries, int fmt, int64_t n_ops, int64_t* n_done,
+                                      cudaStream_t st) {
+    *n_done = 0;
+    if (n_ops == 0) return cudaSuccess;
+    const int blocks = probe_blocks();
+    const int64_t pt = per_thread_of(n_ops, blocks * 256);
+    *n_done = pt * blocks * 256;
+    if (fmt == 1)
+        k_random_red16<1><<<blocks, 256, 0, st>>>(table, (uint32_t)(n_entries - 1), pt);
+    else
+        k_random_red16<2><<<blocks, 256, 0, st>>>(table, (uint32_t)(n_entries - 1), pt);
     return cudaGetLastError();
 }
 

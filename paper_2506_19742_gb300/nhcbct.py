@@ -112,6 +112,7 @@ _SIGS = {
     "probe_l2_read": (_I, [_P, C.c_uint64, _I, _P, _P]),
     "probe_random_gather": (_I, [_P, C.c_uint64, _I, C.c_int64, _P, C.POINTER(C.c_int64), _P]),
     "probe_random_red": (_I, [_P, C.c_uint64, C.c_int64, C.POINTER(C.c_int64), _P]),
+    "probe_random_red16": (_I, [_P, C.c_uint64, _I, C.c_int64, C.POINTER(C.c_int64), _P]),
 }
 EXPORTS = tuple(_SIGS)
 
@@ -576,6 +577,16 @@ def probe_random_red(table, n_ops, stream=None):
     done = C.c_int64()
     _check(load().probe_random_red(_ptr(table), table.numel() // 2, int(n_ops), C.byref(done), _stream(stream)),
            "probe_random_red")
+    return done.value
+
+
+def probe_random_red16(table, fmt, n_ops, stream=None):
+    """Random packed 16-bit atomic adds (fmt PREC_BF16 or PREC_F16) into the 4-byte
+    entries of table (any dtype, 4-byte aligned); returns the count issued."""
+    done = C.c_int64()
+    n_entries = table.numel() * table.element_size() // 4
+    _check(load().probe_random_red16(_ptr(table), n_entries, int(fmt), int(n_ops), C.byref(done),
+                                     _stream(stream)), "probe_random_red16")
     return done.value
 
 
