@@ -568,24 +568,36 @@ __device__ __forceinline__ void mma_forward(const FieldArgs& fa, const float* sp
     frag_st(tslot0 + 32 + 16 * fa.H, C);
 }
 
-template <int D, int G, typename TT>
+// With COOP (the fused training kernel) every warp of the CTA calls this in every
+// round and the MLP weight gradient is the CTA-cooperative one (nh_field_mma.cuh); a
+// warp whose ray misses the volume (co.live false) only takes part in it.
+template <int D, int G, typename TT, bool COOP = false>
 __device__ __forceinline__ void mma_backward(const FieldArgs& fa, const float* sp, const uint16_t* sw,
                                              const float* smask, float* sg, float* wbuf, uint32_t tslot0,
                                              const float x[3], bool active, int lane, const MmaCarry<D, G>& s,
-                                             float dmu) {
+                                             float dmu, const CoopArgs& co = CoopArgs{nullptr, 0, 0, 0, true}) {
     const DenseLayout lay{D, fa.H};
     uint16_t* tile = reinterpret_cast<uint16_t*>(wbuf);
     uint16_t* dztile = tile + kTile16;
     float* rowbuf = reinterpret_cast<float*>(dztile + kTile16);
+    const bool live = !COOP || co.live;
     const float dzo = dmu * s.mu * (1.f - s.mu);
     float dz[2][4][4];
-    {
+    if (live) {
         float C[2][4][4];
         frag_ld(tslot0 + 32 + 16 * fa.H, C);
         out_layer_backward_mma<4>(lay, sp, sg, rowbuf, lane, dzo, C, dz);
+    } else {
+#pragma unroll
+        for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+            for (int nt = 0; nt < 4; nt++)
+#pragma unroll
+                for (int c = 0; c < 4; c++) dz[mt][nt][c] = 0.f;
     }
     float dh[D];
-    mlp_backward_mma<TT, D>(lay, sw, sg, tile, dztile, lane, tslot0 + 32, dz, dh);
+    mlp_backward_mma<TT, D, COOP>(lay, sw, sg, tile, dztile, lane, tslot0 + 32, dz, dh, co);
+    if (!live) return;
     float hhat[D];
     tmem_ld(tslot0, hhat);
     nhe_backward_scatter<D, G>(fa, sp, smask, sg, wbuf, hhat, s.rstd, dh, x, active, lane);
@@ -754,7 +766,9 @@ struct TrainCarry<D, G, __half> {
 // NW: most warps a CTA launches with. CTAs of at most six warps (rays of three,
 // five or six chunks) are compiled with the register budget of two six-warp CTAs
 // per SM instead of two eight-warp ones; CTAs of 9..16 warps (one long ray each)
-// run one per SM.
+// run one per SM. On the 16-bit path the six-warp CTAs (5 or 6 warps launched)
+// take the CTA-cooperative MLP weight gradient; the larger CTAs, compiled for 128
+// registers, keep the per-warp shared atomics, which need fewer registers.
 template <int D, int G, typename TT, int NW>
 __global__ void __launch_bounds__(NW * 32, NW > 8 ? 1 : 2)
 k_ray_train(FieldArgs fa, ViewArgs va, const int32_t* __restrict__ pix, const float* __restrict__ a_meas, int R,
@@ -815,14 +829,20 @@ k_ray_train(FieldArgs fa, ViewArgs va, const int32_t* __restrict__ pix, const fl
         __syncthreads();
         if (threadIdx.x == 0)
             for (int t = 0; t < rpr && grp * rpr + t < R; t++) s_loss += s_lr[t];
-        if (work) {
-            const float dmu = active ? s_g[rl] * g.delta : 0.f;
-            if constexpr (kMmaPath<TT>)
-                mma_backward<D, G, TT>(fa, cta.sp, cta.sw, cta.smask, cta.sg, cta.wbuf, cta.tslot0, x, active, lane, st,
-                                    dmu);
-            else
-                f32_backward<D, G, TT>(fa, cta.sp, cta.smask, cta.sg, cta.wbuf, cta.tslot0, x, active, lane,
-                                        st, dmu);
+        const float dmu = active ? s_g[rl] * g.delta : 0.f;
+        if constexpr (kMmaPath<TT>) {
+            if constexpr (NW <= 6) {
+                // every warp takes part in the cooperative weight gradient, work or not
+                const int wf = bwd_warp_floats(fa.precision);
+                const CoopArgs co{cta.wbuf - warp * wf, wf, (int)(blockDim.x >> 5), warp, work};
+                mma_backward<D, G, TT, true>(fa, cta.sp, cta.sw, cta.smask, cta.sg, cta.wbuf, cta.tslot0, x, active,
+                                             lane, st, dmu, co);
+            } else if (work) {
+                mma_backward<D, G, TT>(fa, cta.sp, cta.sw, cta.smask, cta.sg, cta.wbuf, cta.tslot0, x, active, lane,
+                                       st, dmu);
+            }
+        } else if (work) {
+            f32_backward<D, G, TT>(fa, cta.sp, cta.smask, cta.sg, cta.wbuf, cta.tslot0, x, active, lane, st, dmu);
         }
     }
     bwd_end(fa, cta, tcols);

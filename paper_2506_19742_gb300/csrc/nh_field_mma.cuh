@@ -153,13 +153,73 @@ __device__ __forceinline__ void add_colsum(const float (&Cf)[2][NT][4], float* s
         }
 }
 
+// CTA-cooperative weight gradient of the fused training kernel: instead of every
+// warp adding its 32-sample partial of dW_l to the CTA accumulator with shared
+// atomics, the CTA's warps first write their dz and input tiles, meet at a named
+// barrier, and warp u computes output unit u = (16-row half mj of j, 16-column
+// group np of i) over all the CTA's samples (K = 32 nw), adding it to the
+// accumulator with plain read-modify-writes: every accumulator element has one
+// owner. Every warp of the CTA takes part in every barrier, including warps whose
+// ray misses the volume (`live` false), which write zero tiles.
+struct CoopArgs {
+    const float* wbuf0;   // warp 0's scratch; warp v's is wbuf0 + v * wf
+    int wf;               // scratch floats per warp
+    int nw;               // warps in the CTA (>= 4 units of work; the kernels launch >= 5)
+    int warp;
+    bool live;            // this warp holds samples of a ray that meets the volume
+};
+
+__device__ __forceinline__ void coop_barrier() {
+    asm volatile("bar.sync 1, %0;\n" :: "r"((int)blockDim.x) : "memory");
+}
+
+template <typename T, int IN>
+__device__ __forceinline__ void coop_wgrad(const CoopArgs& co, float* gW, int lane) {
+    constexpr int NP = IN / 16;
+    const int u = co.warp;
+    if (u >= 2 * NP) return;
+    const int mj = u / NP, np = u - mj * NP;
+    const int g = lane >> 2, t = lane & 3;
+    const int q = lane >> 3, r8 = lane & 7;
+    float dW[2][4];
+#pragma unroll
+    for (int h = 0; h < 2; h++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) dW[h][c] = 0.f;
+#pragma unroll 1
+    for (int v = 0; v < co.nw; v++) {
+        const uint16_t* vt = reinterpret_cast<const uint16_t*>(co.wbuf0 + v * co.wf);
+        const uint16_t* vdz = vt + kTile16;
+#pragma unroll
+        for (int ks = 0; ks < 2; ks++) {
+            uint32_t AdT[4], Bq[4];
+            ldsm_x4_trans(AdT, vdz + (16 * ks + (q >> 1) * 8 + r8) * kWS + 16 * mj + (q & 1) * 8);
+            ldsm_x4_trans(Bq, vt + (16 * ks + (q & 1) * 8 + r8) * kWS + 16 * np + (q >> 1) * 8);
+            Mma<T>::mma(dW[0], AdT, Bq[0], Bq[1]);
+            Mma<T>::mma(dW[1], AdT, Bq[2], Bq[3]);
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; h++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            const int j = 16 * mj + g + 8 * (c >> 1), i = 8 * (2 * np + h) + 2 * t + (c & 1);
+            gW[j * IN + wswz(i, j, IN)] += dW[h][c];
+        }
+}
+
 // Backward of the mixed-precision MLP for the warp's 32 samples. dz enters as the
 // gradient at the last hidden layer's pre-activation (f32 fragments); dy leaves as
 // this lane's row of dL/dy (the LN output), D floats.
-template <typename T, int D>
+// With COOP (the fused training kernel only) the weight gradient is the
+// CTA-cooperative one above and every warp of the CTA must call this function in
+// every round; a warp with live == false passes dz = 0 and contributes zero tiles.
+template <typename T, int D, bool COOP = false>
 __device__ __forceinline__ void mlp_backward_mma(const DenseLayout& lay, const uint16_t* sw, float* sg,
                                                  uint16_t* tile, uint16_t* dztile, int lane, uint32_t tcol0,
-                                                 float (&dz)[2][4][4], float (&dy)[D]) {
+                                                 float (&dz)[2][4][4], float (&dy)[D],
+                                                 const CoopArgs& co = CoopArgs{nullptr, 0, 0, 0, true}) {
+    const bool live = !COOP || co.live;
     const int g = lane >> 2, t = lane & 3;
     const int q = lane >> 3, r8 = lane & 7;
 #pragma unroll 1
@@ -170,13 +230,25 @@ __device__ __forceinline__ void mlp_backward_mma(const DenseLayout& lay, const u
         const int IN = first ? D : kW;
         // db_l; dz as hi + lo 16-bit fragments: the data gradient uses both (so the
         // rounding does not compound along the chain), the dz tile holds hi
-        add_colsum<4>(dz, sg + lay.b(l), lane);
+        if (live) add_colsum<4>(dz, sg + lay.b(l), lane);
         uint32_t Adz[2][2][4], Adl[2][2][4];
         pack_afrag_split<T>(dz, Adz, Adl);
         {
             // layer input fragments from tensor memory into the activation tile
             uint32_t Aact[2][2][4];
-            tm_ld_u32<16>(tcol0 + 16 * l, &Aact[0][0][0]);
+            if (live) {
+                tm_ld_u32<16>(tcol0 + 16 * l, &Aact[0][0][0]);
+            } else {
+#pragma unroll
+                for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+                    for (int ks = 0; ks < 2; ks++)
+#pragma unroll
+                        for (int r = 0; r < 4; r++) Aact[mt][ks][r] = 0u;
+            }
+            if constexpr (COOP) {
+                if (l < lay.H - 1) coop_barrier();   // every warp's reads of layer l + 1's tiles are done
+            }
             __syncwarp();
             store_afrag<2>(dztile, lane, Adz);
             if (first && D == 16) {
@@ -191,6 +263,11 @@ __device__ __forceinline__ void mlp_backward_mma(const DenseLayout& lay, const u
             }
             __syncwarp();
         }
+        if constexpr (COOP) {
+            coop_barrier();   // every warp's tiles of layer l are written
+            if (first) coop_wgrad<T, D>(co, sg + lay.W(l), lane);
+            else coop_wgrad<T, kW>(co, sg + lay.W(l), lane);
+        } else {
         // dW_l[j][i] = sum_s dz[s][j] act[s][i]: A = dz^T (m = j, k = s), B = act (k = s, n = i),
         // one 16-row half of j at a time
         {
@@ -233,6 +310,13 @@ __device__ __forceinline__ void mlp_backward_mma(const DenseLayout& lay, const u
                 }
             }
         }
+        }
+        if (!live) {
+            if constexpr (COOP) {
+                if (first) coop_barrier();   // matches the barrier before the dy rows below
+            }
+            continue;
+        }
         // data gradient din[s][i] = sum_j dz[s][j] W[j][i] (B = W^T rows), from the
         // hi and lo parts of dz so that the rounding does not compound along the chain
         float din[2][4][4];
@@ -267,6 +351,7 @@ __device__ __forceinline__ void mlp_backward_mma(const DenseLayout& lay, const u
                 }
         } else {
             // dy rows: fragments -> float tile [32][D + 2] -> this lane's row
+            if constexpr (COOP) coop_barrier();   // every warp's reads of layer 0's tiles are done
             __syncwarp();
             float* ft = reinterpret_cast<float*>(tile);
             constexpr int SF = D + 2;

@@ -147,10 +147,10 @@ def fp32_gradient_errors(g, g_ref, cfg, cache, dLdA, tol=1e-3):
 
     Dense groups (gamma, beta, W_k, b_k): every entry within tol of the group's
     largest entry. Hash tables: the entries that no ReLU-ambiguous sample reaches
-    (see table_kink_allowance) within tol of the largest table entry; every entry
-    within tol of it plus the kink allowance; and the error norm within tol of the
-    table gradient's norm. Returns {group: (max error / max |ref|, error norm /
-    ref norm)} of the failing groups, and prints every group's errors."""
+    (see table_kink_allowance) within tol of the largest table entry, and their
+    error norm within tol of the table gradient's norm; every entry within tol of
+    the largest entry plus the kink allowance. Returns {group: errors} of the
+    failing groups, and prints every group's errors."""
     lay = S.param_layout(cfg)
     allow = table_kink_allowance(cache, dLdA, cfg)
     names = ("tables", "gamma", "beta") + tuple(f"{p}{k}" for k in range(cfg.hidden_layers + 1) for p in ("W", "b"))
@@ -168,7 +168,8 @@ def fp32_gradient_errors(g, g_ref, cfg, cache, dLdA, tol=1e-3):
         if name == "tables":
             al = allow[o:o + n]
             strict = al == 0
-            err = (d[strict].max() / scale, err[1], float(np.max(d - al) / scale), float(np.mean(~strict)))
+            err = (d[strict].max() / scale, float(np.linalg.norm(d[strict]) / np.linalg.norm(b)),
+                   float(np.max(d - al) / scale), float(np.mean(~strict)))
             ok = err[0] <= tol and err[1] <= tol and err[2] <= tol
         else:
             ok = err[0] <= tol

@@ -210,12 +210,14 @@ def test_train_step_loss_and_gradients_match_oracle(lib, case, loss):
 
 
 @pytest.mark.parametrize("precision", [S.PREC_F32, S.PREC_BF16])
-@pytest.mark.parametrize("N", [64, 192, 300, 512, 520])
+@pytest.mark.parametrize("N", [64, 80, 150, 192, 300, 512, 520])
 def test_train_step_fused_and_split_paths_match_oracle(lib, precision, N):
     """accumulate_step runs one fused forward+loss+backward kernel when a ray has at
     most 16 chunks of 32 samples (N <= 512: several rays per CTA up to 8 chunks, one
     ray per CTA for N = 300 and the largest fused ray, N = 512) and separate kernels
-    otherwise (N = 520). Each gives the oracle's loss (FP32 within 1e-5) and every
+    otherwise (N = 520). N = 80 (two rays of 3 chunks per 6-warp CTA), 150 (one ray
+    of 5 chunks) and 192 (6 chunks) take the 16-bit path's CTA-cooperative weight
+    gradient, with rays that miss the volume in the batch. Each gives the oracle's loss (FP32 within 1e-5) and every
     gradient group element by element (FP32 within 1e-3 of the group's largest
     entry, BF16 within the mixed norm bound); train_step then gives the same loss,
     applies Adam and zeroes the gradients."""
