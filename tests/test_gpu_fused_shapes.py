@@ -22,10 +22,11 @@ sums). A ReLU unit whose pre-activation lies within float32 rounding of zero may
 take either branch, and at these batch sizes a handful of such units moves single
 table entries by up to a few 1e-3 of the largest one; so the table entries those
 samples reach are held to the 1e-3 bound plus the bound on that effect
-(_cases.table_kink_allowance), all others to 1e-3, and the table's error norm to
-1e-3 of its norm (_cases.fp32_gradient_errors). 16-bit tables and tensor-core MLP within the derived mixed-precision bounds
-(forward 15u / 25u of the largest A, gradient error norm 2 sqrt(u) of the group's
-norm; u = 2^-9 BF16, 2^-12 FP16). The C2 shape at the full 2048-ray batch is in
+(_cases.table_kink_allowance), all others to 1e-3, with their error norm within
+1e-3 of the table gradient's norm (_cases.fp32_gradient_errors). 16-bit tables and
+the tensor-core MLP stay within the derived mixed-precision bounds (forward 15u /
+25u of the largest A, gradient error norm 2 sqrt(u) of the group's norm;
+u = 2^-9 BF16, 2^-12 FP16). The C2 shape at the full 2048-ray batch is in
 test_gpu_parity.py (test_full_size_fused_step_matches_oracle).
 """
 import numpy as np

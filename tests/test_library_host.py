@@ -317,3 +317,28 @@ def test_channel_mask_selection_validation_rejects_before_any_launch(nh):
     assert sel(h, 64, 0.25, 0.85, 1, fake, fake, fake + 128, need.value, None) == -7
     assert sel(h, 64, 0.25, 0.85, 1, fake, fake, fake, need.value - 1, None) == -3
     lib.field_destroy(h)
+
+
+def test_roofline_probe_validation_rejects_before_any_launch(nh):
+    """Host checks of the roofline probes (random gather, float2 and packed 16-bit
+    reductions, streaming read): null, non-power-of-two, oversized, misaligned and
+    wrong-format arguments return their status codes without touching the (fake)
+    device addresses."""
+    lib = nh.load()
+    fake = 1 << 40
+    done = C.c_int64()
+    assert lib.probe_random_red16(None, 1 << 20, 1, 1024, C.byref(done), None) == -1
+    assert lib.probe_random_red16(fake, 1 << 20, 1, 1024, None, None) == -1
+    assert lib.probe_random_red16(fake, 3 << 20, 1, 1024, C.byref(done), None) == -1
+    assert lib.probe_random_red16(fake, 1 << 33, 2, 1024, C.byref(done), None) == -1
+    assert lib.probe_random_red16(fake, 1 << 20, 0, 1024, C.byref(done), None) == -1   # FP32 is not packed
+    assert lib.probe_random_red16(fake, 1 << 20, 1, -1, C.byref(done), None) == -1
+    assert lib.probe_random_red16(fake + 2, 1 << 20, 2, 1024, C.byref(done), None) == -7
+    assert lib.probe_random_red(fake, 1 << 20, 1024, None, None) == -1
+    assert lib.probe_random_red(fake, 1000, 1024, C.byref(done), None) == -1
+    assert lib.probe_random_red(fake + 4, 1 << 20, 1024, C.byref(done), None) == -7
+    assert lib.probe_random_gather(fake, 1 << 20, 6, 1024, fake, C.byref(done), None) == -1
+    assert lib.probe_random_gather(fake + 4, 1 << 20, 8, 1024, fake, C.byref(done), None) == -7
+    assert lib.probe_l2_read(fake, 1000, 1, fake, None) == -1
+    assert lib.probe_l2_read(fake + 8, 1024, 1, fake, None) == -7
+    assert lib.probe_l2_read(fake, 1024, 0, fake, None) == -1
