@@ -605,9 +605,9 @@ def test_splitmix64_reference_outputs_and_jittered_strata():
         assert np.all(s > np.arange(9) - 1e-3) and np.all(s < np.arange(9) + 1 + 1e-3)
 
 
-# ---------------------------------------------------------------- stored record
+# ---------------------------------------------------------------- measurement model
 def test_poisson_measurement_has_the_poisson_moments_and_the_count_floor():
-    """Measured projections (Sec. 3.1; the measurement model of the north-star
+    """Measured projections (Sec. 3.1; the measurement model of the benchmark
     workloads): I ~ Poisson(I0 exp(-A)), A_meas = -ln(max(I, 1) / I0). The counts
     recovered from A_meas must have the Poisson mean and variance lambda = I0 e^-A
     (each within 5 standard errors over 200 000 draws), A_meas must centre on A
@@ -635,6 +635,7 @@ def test_poisson_measurement_has_the_poisson_moments_and_the_count_floor():
     assert not np.array_equal(S.poisson_measure(a, I0, 9), S.poisson_measure(a, I0, 10))
 
 
+# ---------------------------------------------------------------- stored record
 def test_oracle_reproduces_its_stored_step():
     """tests/golden/oracle_step.json (written by tests/golden/make_golden.py from the
     oracle alone) still matches the oracle: a change to the oracle's arithmetic shows
