@@ -15,6 +15,11 @@ below cover the per-level normalization (D = 16, G = 8) and the one-group LN
 | large (C4) | L16 T2^21 BF16 | 256 | 8 | 1 | 8 |
 | paper320 (Sec. 3.1 step, L1) | L16 T2^19 | 320 | 10 | 1 | 10 |
 | 16 warps | L16 T2^19 | 512 | 16 | 1 | 16 |
+| 5 warps, FP16 tables | L16 T2^19 FP16, loss scale 1024 | 160 | 5 | 1 | 5 |
+
+Six-warp and five-warp CTAs on the 16-bit path take the CTA-cooperative MLP
+weight gradient (paper_bf16 at N = 192 in test_gpu_parity.py, FP16 at N = 160
+here); the others the per-warp shared atomics.
 
 Tolerances: the loss within 1e-5 relative in FP32 (the stated forward bound); each
 FP32 gradient group within 1e-3 of its largest entry (scatter atomics reorder the
@@ -55,6 +60,7 @@ SHAPES = [
     ("paper_fp32_n512", "paper_fp32", 256, 512, {}),
     ("paper_bf16_n512", "paper_bf16", 256, 512, {}),
     ("paper_fp32_n256", "paper_fp32", 512, 256, {}),
+    ("paper_f16_n160", "paper_bf16", 512, 160, {"precision": S.PREC_F16, "loss_scale_init": 1024.0}),
 ]
 
 
