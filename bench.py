@@ -61,7 +61,8 @@ def parse_args():
     p.add_argument("--no-mci", action="store_true", help="skip the compact MCI block of the default run")
     p.add_argument("--psnr-steps", type=int, default=3000, help="step cap of the time-to-PSNR runs")
     p.add_argument("--experiment", default="", choices=["", "mci", "fftmask", "variants", "ablation", "variation",
-                                                          "views"])
+                                                          "views", "precision"])
+    p.add_argument("--precision-seeds", type=int, default=5, help="precision: scans (seeds) to train")
     p.add_argument("--views", default="10,25,50,100", help="views: comma-separated view counts")
     p.add_argument("--variation-steps", type=int, default=1500, help="variation: training steps per arm")
     p.add_argument("--mask-step", type=int, default=500, help="fftmask: step at which the mask is chosen")
@@ -738,6 +739,51 @@ def run_variation(args):
     print(json.dumps(out))
 
 
+def run_precision(args):
+    """The mixed-precision target on several scans: for each of --precision-seeds
+    seeds, the paper-scale scan trained from the same initialisation and batches in
+    FP32 (twice), in BF16 and in FP16 (with its dynamic loss scale) for --psnr-steps
+    steps; final PSNR and 3-D SSIM, steps and seconds to 30 dB, and the per-seed and
+    mean final-PSNR differences to the first FP32 run. Hash-gradient atomics add in
+    no fixed order, so one run per seed is one draw; the second FP32 run measures
+    that run-to-run spread against which the precisions are compared."""
+    import dataclasses
+    import torch
+    from paper_2506_19742_gb300 import build as nhbuild
+    from paper_2506_19742_gb300 import channel_mask as cm
+    from paper_2506_19742_gb300 import nhcbct as nh
+    from paper_2506_19742_gb300 import recon
+    nhbuild.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    base = S.WORKLOADS[args.workload]
+    arms = {"fp32": base,
+            "fp32_repeat": base,
+            "bf16": dataclasses.replace(base, field=dataclasses.replace(base.field, precision=S.PREC_BF16)),
+            "f16": dataclasses.replace(base, field=dataclasses.replace(base.field, precision=S.PREC_F16,
+                                                                        loss_scale_init=1024.0,
+                                                                        growth_interval=200))}
+    out = {"experiment": "precision", "workload": base.name, "steps": args.psnr_steps, "seeds": []}
+    for k in range(args.precision_seeds):
+        seed = 300 + k
+        scan = make_scan(nh, torch, base, seed, dev)
+        row = {"seed": seed}
+        for name, w in arms.items():
+            r = train_arm(nh, torch, recon, cm, w, scan, seed, args.psnr_steps)
+            row[name] = {kk: r[kk] for kk in ("final_psnr", "best_psnr", "final_ssim", "steps_to", "seconds_to",
+                                              "ms_per_step")}
+        for name in ("fp32_repeat", "bf16", "f16"):
+            row[name]["final_psnr_delta_db"] = round(row[name]["final_psnr"] - row["fp32"]["final_psnr"], 3)
+        out["seeds"].append(row)
+        del scan
+    for name in ("fp32_repeat", "bf16", "f16"):
+        d = np.array([r[name]["final_psnr_delta_db"] for r in out["seeds"]])
+        out[name + "_final_psnr_delta_db"] = {"mean": round(float(d.mean()), 3), "std": round(float(d.std()), 3),
+                                               "min": round(float(d.min()), 3), "max": round(float(d.max()), 3),
+                                               "within_0.1": int(np.sum(np.abs(d) <= 0.1))}
+    print(json.dumps(out))
+
+
 def run_fftmask(args):
     """FFT channel masking (Sec. 2.3) on the benchmark scan: the same initialisation
     and batches trained with no mask, and with the mask chosen from the hash
@@ -1130,6 +1176,9 @@ def main():
     elif args.experiment == "views":
         if rank == 0:
             run_views(args)
+    elif args.experiment == "precision":
+        if rank == 0:
+            run_precision(args)
     elif args.impl == "reference":
         run_reference(args, rank, world)
     else:
