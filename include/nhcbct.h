@@ -204,6 +204,12 @@ nh_status field_poll_status(nh_field* f, void* stream, uint32_t* flags, float* l
  * seed per step draws new ones. Rays that miss the volume predict A = 0 and
  * contribute no gradient.
  * pix: device int32[n_rays]; a_meas: device float[n_rays] (may be NULL where unused).
+ * The result does not depend on the order of the rays in a batch beyond float
+ * rounding, but the order sets which rays run side by side: pixels in ascending
+ * id (detector raster order) put neighbouring rays, which read and update
+ * neighbouring table entries, on the GPU at the same time and so raise the L2
+ * hit rate. The fused step then runs about 6 % faster (paper-size FP32 field) to
+ * 8 % faster (tables larger than the L2) than with the same pixels shuffled.
  */
 typedef struct {
     int32_t        view;

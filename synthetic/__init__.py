@@ -277,11 +277,15 @@ def pick_rays(rng: np.random.Generator, n_views: int, candidates, R: int):
 
     ``candidates[v]`` lists the pixel ids (row * nu + col) of view v that a batch may
     use, normally those whose ray meets the volume, so that every ray carries samples.
+    The drawn pixels come back in ascending id (detector raster order). The loss and
+    the gradients do not depend on the order beyond float rounding, but rays that sit
+    next to each other in the batch run side by side on the GPU, and neighbouring rays
+    touch neighbouring table entries, which the L2 then serves.
     """
     view = int(rng.integers(0, n_views))
     cand = np.asarray(candidates[view])
     sel = rng.choice(len(cand), size=R, replace=(R > len(cand)))
-    return view, cand[sel].astype(np.int32)
+    return view, np.sort(cand[sel]).astype(np.int32)
 
 
 def poisson_measure(A_clean: np.ndarray, I0: float, seed: int) -> np.ndarray:
