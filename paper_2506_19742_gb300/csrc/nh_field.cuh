@@ -414,9 +414,10 @@ __device__ __forceinline__ void affine_row(const FieldArgs& fa, const float* sp,
 // Forward of one sample per lane, the MLP on tensor cores (nh_field_tf32.cuh). All 32
 // lanes must call it together. Warp scratch: the input tile (wbuf) and the dz tile
 // (wbuf + 32 x 32), the latter also the output layer's row buffer.
-template <int D, int G, typename TT>
-__device__ __forceinline__ void f32_forward(const FieldArgs& fa, const float* sp, const float* smask, float* wbuf,
-                                            uint32_t tslot0, const float x[3], int lane, F32Carry<D, G>& s) {
+template <int D, int G, typename TT, bool PS = false>
+__device__ __forceinline__ void f32_forward(const FieldArgs& fa, const float* sp, const float* wlo, const float* smask,
+                                            float* wbuf, uint32_t tslot0, const float x[3], int lane,
+                                            F32Carry<D, G>& s) {
     constexpr int L = D / 2;
     const DenseLayout lay{D, fa.H};
     const int H = fa.H;
@@ -432,14 +433,14 @@ __device__ __forceinline__ void f32_forward(const FieldArgs& fa, const float* sp
         __syncwarp();   // the gather's reads of the tile are done
         row_to_tile<D>(act, lane, y);
         __syncwarp();
-        tf32_layer_tile<D / 8>(act, sp + lay.W(0), sp + lay.b(0), lane, z);
+        tf32_layer_tile<D / 8, PS>(act, sp + lay.W(0), wlo, sp + lay.b(0), lane, z);
     }
     float a[2][4][4];
 #pragma unroll 1
     for (int k = 1; k < H; k++) {
         relu_frag<4>(z, a);
         frag_tmem_st(tslot0 + 32 * k, a);
-        tf32_layer_frag(a, sp + lay.W(k), sp + lay.b(k), lane, z);
+        tf32_layer_frag<PS>(a, sp + lay.W(k), wlo + k * kW * kW, sp + lay.b(k), lane, z);
     }
     relu_frag<4>(z, a);
     s.mu = tf32_out_forward(sp + lay.W(H), sp[lay.b(H)], a, dzt, lane);
@@ -449,10 +450,11 @@ __device__ __forceinline__ void f32_forward(const FieldArgs& fa, const float* sp
 
 // Backward of one sample per lane given dL/dmu (already multiplied by the loss
 // scale; 0 for lanes without a sample). All 32 lanes must call it together.
-template <int D, int G, typename TT>
-__device__ __forceinline__ void f32_backward(const FieldArgs& fa, const float* sp, const float* smask, float* sg,
-                                             float* wbuf, uint32_t tslot0, const float x[3], bool active, int lane,
-                                             const F32Carry<D, G>& s, float dmu) {
+template <int D, int G, typename TT, bool PS = false>
+__device__ __forceinline__ void f32_backward(const FieldArgs& fa, const float* sp, const float* wlo,
+                                             const float* smask, float* sg, float* wbuf, uint32_t tslot0,
+                                             const float x[3], bool active, int lane, const F32Carry<D, G>& s,
+                                             float dmu) {
     const DenseLayout lay{D, fa.H};
     const int H = fa.H;
     float* act = wbuf;
@@ -479,7 +481,7 @@ __device__ __forceinline__ void f32_backward(const FieldArgs& fa, const float* s
         }
         tf32_wgrad<kW>(dzt, act, sg + lay.W(k), lane);
         float din[2][4][4];
-        tf32_dgrad<4>(dz, sp + lay.W(k), lane, din);
+        tf32_dgrad<4, PS>(dz, sp + lay.W(k), wlo + k * kW * kW, lane, din);
         float a[2][4][4];
         frag_tmem_ld(tslot0 + 32 * k, a);
 #pragma unroll
@@ -505,7 +507,7 @@ __device__ __forceinline__ void f32_backward(const FieldArgs& fa, const float* s
     float dh[D];
     {
         float din[2][D / 8][4];
-        tf32_dgrad<D / 8>(dz, sp + lay.W(0), lane, din);
+        tf32_dgrad<D / 8, PS>(dz, sp + lay.W(0), wlo, lane, din);
         __syncwarp();   // the weight gradient's reads of the input tile are done
         frag_to_tile<D / 8>(act, lane, din);
         __syncwarp();
@@ -520,8 +522,9 @@ __device__ __forceinline__ float sample_fwd_bwd(const FieldArgs& fa, const float
                                                 float* wbuf, uint32_t tslot0, const float x[3], bool active,
                                                 int lane, DmuFn dmu_of) {
     F32Carry<D, G> s;
-    f32_forward<D, G, TT>(fa, sp, smask, wbuf, tslot0, x, lane, s);
-    f32_backward<D, G, TT>(fa, sp, smask, sg, wbuf, tslot0, x, active, lane, s, active ? dmu_of(s.mu) : 0.f);
+    f32_forward<D, G, TT>(fa, sp, nullptr, smask, wbuf, tslot0, x, lane, s);
+    f32_backward<D, G, TT>(fa, sp, nullptr, smask, sg, wbuf, tslot0, x, active, lane, s,
+                           active ? dmu_of(s.mu) : 0.f);
     return s.mu;
 }
 
@@ -637,10 +640,15 @@ __host__ __device__ inline int bwd_warp_floats(int precision) {
     return precision == NH_PREC_F32 ? warp_scratch_floats() : kMmaWarpFloats;
 }
 
+// FP32 training CTAs of at most this many warps split the MLP weights once at
+// staging (the lo tiles, H kW kW floats, still leave room for two CTAs per SM).
+constexpr int kPresplitMaxWarps = 6;
+
 static size_t bwd_smem_bytes(const FieldArgs& fa, int nwarps = kBwdWarps) {
     const int ndp = (fa.n_dense + 3) & ~3;
     size_t b = (size_t)(2 * ndp + kMaxD + nwarps * bwd_warp_floats(fa.precision)) * sizeof(float);
     if (fa.precision != NH_PREC_F32) b += (size_t)fa.H * kMmaLayerElems * 2;
+    else if (nwarps <= kPresplitMaxWarps) b += (size_t)fa.H * kW * kW * sizeof(float);
     if (512u / bwd_tmem_cols(fa, nwarps) < 2u && b < 120 * 1024) b = 120 * 1024;
     return b;
 }
@@ -649,10 +657,12 @@ static size_t bwd_smem_bytes(const FieldArgs& fa, int nwarps = kBwdWarps) {
 struct BwdCta {
     float *sp, *smask, *sg, *wbuf;
     const uint16_t* sw;   // 16-bit path: W and W^T per layer
+    float* wlo;           // FP32 path with split weights: the lo tiles, else null
     uint32_t tbase, tslot0;
 };
 
-template <typename TT>
+// PS: stage the FP32 weights split (the CTA was sized for the lo tiles).
+template <typename TT, bool PS = false>
 __device__ __forceinline__ BwdCta bwd_begin(const FieldArgs& fa, float* smem, uint32_t* s_tmem, uint32_t tcols) {
     BwdCta c;
     const int ndp = (fa.n_dense + 3) & ~3;
@@ -664,6 +674,7 @@ __device__ __forceinline__ BwdCta bwd_begin(const FieldArgs& fa, float* smem, ui
     c.wbuf = c.sg + ndp + warp * wf;
     uint16_t* sw = reinterpret_cast<uint16_t*>(c.sg + ndp + (int)(blockDim.x >> 5) * wf);
     c.sw = sw;
+    c.wlo = (!kMmaPath<TT> && PS) ? reinterpret_cast<float*>(sw) : nullptr;
     if (warp == 0) tmem_alloc(s_tmem, tcols);
     load_dense(fa, c.sp, c.smask);
     for (int k = threadIdx.x; k < ndp; k += blockDim.x) c.sg[k] = 0.f;
@@ -671,7 +682,7 @@ __device__ __forceinline__ BwdCta bwd_begin(const FieldArgs& fa, float* smem, ui
     if constexpr (kMmaPath<TT>)
         stage_weights16<TT>(c.sp, DenseLayout{fa.D, fa.H}, fa.D, sw);
     else
-        stage_wt_tf32(fa.params + fa.n_table, DenseLayout{fa.D, fa.H}, fa.D, c.sp);
+        stage_wt_tf32(fa.params + fa.n_table, DenseLayout{fa.D, fa.H}, fa.D, c.sp, c.wlo);
     tmem_fence_before_sync();
     __syncthreads();
     tmem_fence_after_sync();
@@ -779,7 +790,8 @@ k_ray_train(FieldArgs fa, ViewArgs va, const int32_t* __restrict__ pix, const fl
     __shared__ float s_g[kMaxTrainWarps];
     __shared__ float s_lr[kMaxTrainWarps];
     __shared__ float s_loss;
-    const BwdCta cta = bwd_begin<TT>(fa, smem, &s_tmem, tcols);
+    constexpr bool PS = NW <= kPresplitMaxWarps;
+    const BwdCta cta = bwd_begin<TT, PS>(fa, smem, &s_tmem, tcols);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int rl = warp / C, c = warp - rl * C;
     const float scale = fa.state->loss_scale;
@@ -803,7 +815,7 @@ k_ray_train(FieldArgs fa, ViewArgs va, const int32_t* __restrict__ pix, const fl
             if constexpr (kMmaPath<TT>)
                 mma_forward<D, G, TT>(fa, cta.sp, cta.sw, cta.smask, cta.wbuf, cta.tslot0, x, lane, st);
             else
-                f32_forward<D, G, TT>(fa, cta.sp, cta.smask, cta.wbuf, cta.tslot0, x, lane, st);
+                f32_forward<D, G, TT, PS>(fa, cta.sp, cta.wlo, cta.smask, cta.wbuf, cta.tslot0, x, lane, st);
         }
         const float part = warp_sum(active ? st.mu : 0.f) * (work ? g.delta : 0.f);
         if (lane == 0) s_part[warp] = part;
@@ -842,7 +854,8 @@ k_ray_train(FieldArgs fa, ViewArgs va, const int32_t* __restrict__ pix, const fl
                                        st, dmu);
             }
         } else if (work) {
-            f32_backward<D, G, TT>(fa, cta.sp, cta.smask, cta.sg, cta.wbuf, cta.tslot0, x, active, lane, st, dmu);
+            f32_backward<D, G, TT, PS>(fa, cta.sp, cta.wlo, cta.smask, cta.sg, cta.wbuf, cta.tslot0, x, active, lane,
+                                       st, dmu);
         }
     }
     bwd_end(fa, cta, tcols);

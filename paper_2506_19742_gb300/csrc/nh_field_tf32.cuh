@@ -22,7 +22,11 @@
 // columns are XOR-swizzled by wtsw, in place of W_l in the CTA's copy of the dense
 // parameters; per warp two 32 x 32 float tiles (tsw swizzle), one for a layer's
 // input rows (or C fragments) and one for dz. The swizzles make fragment-pattern
-// loads and stores conflict-free.
+// loads and stores conflict-free. The weights are constant within a launch, so
+// where shared memory allows (PS), the CTA splits each of them once at staging:
+// the W^T tile then holds hi and a second tile of the same layout holds lo, and
+// the products read both halves instead of splitting the weight at every use
+// (the same bits either way).
 #pragma once
 #include <stdint.h>
 
@@ -59,14 +63,27 @@ __device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], 
 }
 
 // c += a b with both operands split: lo_a hi_b + hi_a lo_b + hi_a hi_b.
-__device__ __forceinline__ void mma3(float (&c)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4],
-                                     const float b0, const float b1) {
-    uint32_t bh0, bl0, bh1, bl1;
-    split_tf32(b0, bh0, bl0);
-    split_tf32(b1, bh1, bl1);
+__device__ __forceinline__ void mma3s(float (&c)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4],
+                                      uint32_t bh0, uint32_t bl0, uint32_t bh1, uint32_t bl1) {
     mma_tf32(c, al, bh0, bh1);
     mma_tf32(c, ah, bl0, bl1);
     mma_tf32(c, ah, bh0, bh1);
+}
+
+// B operand pair (b0, b1) of a weight tile at elements e0, e1: split here, or
+// (PS) read as hi from the W^T tile and lo from the lo tile.
+template <bool PS>
+__device__ __forceinline__ void wt_operand(const float* Wt, const float* Wlo, int e0, int e1, uint32_t& bh0,
+                                           uint32_t& bl0, uint32_t& bh1, uint32_t& bl1) {
+    if constexpr (PS) {
+        bh0 = __float_as_uint(Wt[e0]);
+        bh1 = __float_as_uint(Wt[e1]);
+        bl0 = __float_as_uint(Wlo[e0]);
+        bl1 = __float_as_uint(Wlo[e1]);
+    } else {
+        split_tf32(Wt[e0], bh0, bl0);
+        split_tf32(Wt[e1], bh1, bl1);
+    }
 }
 
 // Split A fragment of k-step ks taken from C fragments (permuted contraction index).
@@ -81,16 +98,25 @@ __device__ __forceinline__ void afrag_from_c(const float (&c)[4], uint32_t (&ah)
 // place of W_l ([32][IN], 32 IN floats) in the CTA's copy of the dense parameters
 // (sp + lay.W(l)), read again from global memory (gdense: the dense block), so the
 // tiles cost no shared memory of their own. Only the training kernels' tensor-core
-// MLP reads sp's W_l (l < H), and only as these tiles.
+// MLP reads sp's W_l (l < H), and only as these tiles. With wlo (kW x kW floats
+// per layer, layer l at wlo + l kW kW) the weights are split here: the tile gets
+// hi = tf32(w) and wlo's tile lo = tf32(w - hi).
 __device__ __forceinline__ void stage_wt_tf32(const float* __restrict__ gdense, const DenseLayout& lay, int D,
-                                              float* sp) {
+                                              float* sp, float* wlo) {
     for (int l = 0; l < lay.H; l++) {
         const int IN = l == 0 ? D : kW;
         const float* W = gdense + lay.W(l);
         float* Wt = sp + lay.W(l);
         for (int e = threadIdx.x; e < 32 * IN; e += blockDim.x) {
             const int j = e / IN, i = e - j * IN;
-            Wt[wtsw(i, j)] = W[e];
+            if (wlo) {
+                uint32_t hi, lo;
+                split_tf32(W[e], hi, lo);
+                Wt[wtsw(i, j)] = __uint_as_float(hi);
+                wlo[l * kW * kW + wtsw(i, j)] = __uint_as_float(lo);
+            } else {
+                Wt[wtsw(i, j)] = W[e];
+            }
         }
     }
 }
@@ -146,10 +172,10 @@ __device__ __forceinline__ void tile_to_row(const float* tile, int lane, float (
 }
 
 // z[s][j] = b[j] + sum_i in[s][i] W[j][i] for the warp's 32 samples, 32 outputs.
-// Input rows from a warp tile (KS = IN / 8 k-steps).
-template <int KS>
-__device__ __forceinline__ void tf32_layer_tile(const float* tile, const float* Wt, const float* bias, int lane,
-                                                float (&z)[2][4][4]) {
+// Input rows from a warp tile (KS = IN / 8 k-steps). Wlo: the lo tile (PS only).
+template <int KS, bool PS>
+__device__ __forceinline__ void tf32_layer_tile(const float* tile, const float* Wt, const float* Wlo,
+                                                const float* bias, int lane, float (&z)[2][4][4]) {
     const int g = lane >> 2, t = lane & 3;
 #pragma unroll
     for (int nt = 0; nt < 4; nt++) {
@@ -174,17 +200,19 @@ __device__ __forceinline__ void tf32_layer_tile(const float* tile, const float* 
         }
 #pragma unroll
         for (int nt = 0; nt < 4; nt++) {
-            const float b0 = Wt[wtsw(8 * ks + 2 * t, 8 * nt + g)];
-            const float b1 = Wt[wtsw(8 * ks + 2 * t + 1, 8 * nt + g)];
+            uint32_t bh0, bl0, bh1, bl1;
+            wt_operand<PS>(Wt, Wlo, wtsw(8 * ks + 2 * t, 8 * nt + g), wtsw(8 * ks + 2 * t + 1, 8 * nt + g), bh0, bl0,
+                           bh1, bl1);
 #pragma unroll
-            for (int mt = 0; mt < 2; mt++) mma3(z[mt][nt], ah[mt], al[mt], b0, b1);
+            for (int mt = 0; mt < 2; mt++) mma3s(z[mt][nt], ah[mt], al[mt], bh0, bl0, bh1, bl1);
         }
     }
 }
 
 // The same with the input in C fragments (32 features, the previous layer's output).
-__device__ __forceinline__ void tf32_layer_frag(const float (&a)[2][4][4], const float* Wt, const float* bias,
-                                                int lane, float (&z)[2][4][4]) {
+template <bool PS>
+__device__ __forceinline__ void tf32_layer_frag(const float (&a)[2][4][4], const float* Wt, const float* Wlo,
+                                                const float* bias, int lane, float (&z)[2][4][4]) {
     const int g = lane >> 2, t = lane & 3;
 #pragma unroll
     for (int nt = 0; nt < 4; nt++) {
@@ -204,18 +232,19 @@ __device__ __forceinline__ void tf32_layer_frag(const float (&a)[2][4][4], const
         for (int mt = 0; mt < 2; mt++) afrag_from_c(a[mt][ks], ah[mt], al[mt]);
 #pragma unroll
         for (int nt = 0; nt < 4; nt++) {
-            const float b0 = Wt[wtsw(8 * ks + 2 * t, 8 * nt + g)];
-            const float b1 = Wt[wtsw(8 * ks + 2 * t + 1, 8 * nt + g)];
+            uint32_t bh0, bl0, bh1, bl1;
+            wt_operand<PS>(Wt, Wlo, wtsw(8 * ks + 2 * t, 8 * nt + g), wtsw(8 * ks + 2 * t + 1, 8 * nt + g), bh0, bl0,
+                           bh1, bl1);
 #pragma unroll
-            for (int mt = 0; mt < 2; mt++) mma3(z[mt][nt], ah[mt], al[mt], b0, b1);
+            for (int mt = 0; mt < 2; mt++) mma3s(z[mt][nt], ah[mt], al[mt], bh0, bl0, bh1, bl1);
         }
     }
 }
 
 // Data gradient din[s][i] = sum_j dz[s][j] W[j][i], NT = IN / 8 output n-tiles; dz in
 // C fragments (32 columns j), B[j][i] = W^T[i][j] read as pairs from the W^T tile.
-template <int NT>
-__device__ __forceinline__ void tf32_dgrad(const float (&dz)[2][4][4], const float* Wt, int lane,
+template <int NT, bool PS>
+__device__ __forceinline__ void tf32_dgrad(const float (&dz)[2][4][4], const float* Wt, const float* Wlo, int lane,
                                            float (&din)[2][NT][4]) {
     const int g = lane >> 2, t = lane & 3;
 #pragma unroll
@@ -231,9 +260,21 @@ __device__ __forceinline__ void tf32_dgrad(const float (&dz)[2][4][4], const flo
         for (int mt = 0; mt < 2; mt++) afrag_from_c(dz[mt][ks], ah[mt], al[mt]);
 #pragma unroll
         for (int nt = 0; nt < NT; nt++) {
-            const float2 b = *reinterpret_cast<const float2*>(Wt + wtsw(8 * nt + g, 8 * ks + 2 * t));
+            const int e = wtsw(8 * nt + g, 8 * ks + 2 * t);
+            const float2 b = *reinterpret_cast<const float2*>(Wt + e);
+            uint32_t bh0, bl0, bh1, bl1;
+            if constexpr (PS) {
+                const float2 bl = *reinterpret_cast<const float2*>(Wlo + e);
+                bh0 = __float_as_uint(b.x);
+                bh1 = __float_as_uint(b.y);
+                bl0 = __float_as_uint(bl.x);
+                bl1 = __float_as_uint(bl.y);
+            } else {
+                split_tf32(b.x, bh0, bl0);
+                split_tf32(b.y, bh1, bl1);
+            }
 #pragma unroll
-            for (int mt = 0; mt < 2; mt++) mma3(din[mt][nt], ah[mt], al[mt], b.x, b.y);
+            for (int mt = 0; mt < 2; mt++) mma3s(din[mt][nt], ah[mt], al[mt], bh0, bl0, bh1, bl1);
         }
     }
 }
