@@ -1001,21 +1001,30 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 "launch_ms": {"forward+loss+backward": round(t_acc, 4), "adam": round(t_adam, 4)},
                 "launch": launch}
 
-    # end to end through the host-buffer entry point (pinned host in, loss out)
+    # end to end through the host-buffer entry point (pinned host in, loss out). Every
+    # step copies its pixels and measurements from pinned host memory and its loss
+    # back to the host, and the host reads every step's loss, one step behind: step
+    # k's loss is read once step k + 1 is enqueued, as a training loop that logs its
+    # loss does, so the GPU does not wait for the host between steps.
     pins = [(v, torch.from_numpy(p).pin_memory(), torch.from_numpy(a).pin_memory()) for v, p, a in host_batches]
-    loss_h = torch.zeros(1).pin_memory()
+    loss_h = [torch.zeros(1).pin_memory() for _ in range(2)]
     for v, p, a in pins[:W]:
-        nh.train_step_host(field, geom, v, p, a, N, loss_h, ws)
+        nh.train_step_host(field, geom, v, p, a, N, loss_h[0], ws)
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    losses = []
-    for v, p, a in pins[W:]:
-        nh.train_step_host(field, geom, v, p, a, N, loss_h, ws)
-        torch.cuda.current_stream().synchronize()      # read the step's loss on the host
-        losses.append(float(loss_h[0]))
+    losses, done = [], []
+    for k, (v, p, a) in enumerate(pins[W:]):
+        nh.train_step_host(field, geom, v, p, a, N, loss_h[k % 2], ws)
+        done.append(torch.cuda.Event())
+        done[k].record(stream)
+        if k >= 1:
+            done[k - 1].synchronize()
+            losses.append(float(loss_h[(k - 1) % 2][0]))
+    done[-1].synchronize()
+    losses.append(float(loss_h[(len(done) - 1) % 2][0]))
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = allmax(max(e0.elapsed_time(e1), (time.perf_counter() - t0) * 1e3))
