@@ -266,7 +266,13 @@ nh_status render_forward_noalloc(const nh_field* f, const nh_geometry* g, const 
  * (features are recomputed, not stored). No optimizer step. */
 nh_status render_backward(nh_field* f, const nh_geometry* g, const nh_ray_batch* b,
                           const float* dLdA_dev, void* ws, size_t ws_bytes, void* stream);
-/* Adam over every parameter with the accumulated grads, then zeroes grads. */
+/* Adam with the accumulated grads, then zeroes grads, over every parameter a step
+ * can reach: all entries of hashed levels, the first (N_l + 1)^3 entries of a dense
+ * level (its float count rounded up to a multiple of 4) and the LN / MLP block.
+ * The other entries of a dense level are never read or written by any step, so
+ * their gradients and moments stay zero and Adam would leave them unchanged; the
+ * optimizer skips them and leaves their values, gradients and moments as they are
+ * (27 % of the vector at T = 2^19 with 16 levels from 16 to 2048). */
 nh_status optimizer_step(nh_field* f, void* stream);
 
 /* MCI pre-training step (Eq. 2): loss = mean |mu_gt - M(x)| over n_pts points

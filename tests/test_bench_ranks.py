@@ -73,3 +73,23 @@ def test_reference_arm_prints_only_on_rank_zero():
     assert r.returncode == 0
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0 and line["cpu_baseline"]["cores"] >= 1
+
+
+def test_adam_roofline_counts_the_parameters_the_optimizer_visits():
+    # bench.py's Adam bytes count the reachable parameters only: every entry of a
+    # hashed level, the first (N_l + 1)^3 entries of a dense level (whole groups of
+    # four floats) and the LN / MLP block, computed here from the oracle's level
+    # resolutions
+    sys.path.insert(0, ROOT)
+    import bench
+    import synthetic as S
+    from oracle.encoding import is_dense, level_resolutions
+    for name in ("tiny_fp32", "paper_fp32", "large_bf16"):
+        f = S.WORKLOADS[name].field
+        T, F = 2 ** f.log2_T, f.n_feat
+        n = S.param_layout(f)["_total"][1] - f.n_levels * T * F
+        for res in level_resolutions(f.n_levels, f.base_res, f.max_res):
+            live = (res + 1) ** 3 if is_dense(res, T) else T
+            n += min(T * F, -(-live * F // 4) * 4)
+        assert bench.optimizer_params(f) == n
+        assert n < S.param_layout(f)["_total"][1]

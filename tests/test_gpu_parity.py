@@ -400,20 +400,65 @@ def test_mixed_precision_voxel_loss_and_query(lib, precision):
     _grad_close(g, ref_grad, cfg, what="mixed voxel loss", norm_rtol=tol_g)
 
 
+def reachable_params(cfg):
+    """Mask of the parameters the optimizer visits: every entry of a hashed level,
+    the first (N_l + 1)^3 entries of a dense level (a corner index there is at most
+    (N_l + 1)^3 - 1), its float count rounded up to a multiple of four, and the
+    LN / MLP block. Every parameter a step can give a gradient is inside."""
+    from oracle.encoding import is_dense, level_resolutions
+    T, F = 2 ** cfg.log2_T, cfg.n_feat
+    n = S.param_layout(cfg)["_total"][1]
+    live = np.zeros(n, dtype=bool)
+    for l, res in enumerate(level_resolutions(cfg.n_levels, cfg.base_res, cfg.max_res)):
+        n_l = (res + 1) ** 3 if is_dense(res, T) else T
+        live[l * T * F: l * T * F + min(T * F, -(-n_l * F // 4) * 4)] = True
+    live[cfg.n_levels * T * F:] = True
+    return live
+
+
 def test_adam_matches_oracle(lib):
+    # gradients on every parameter a step can reach (this field has dense levels
+    # with unreachable entries, which the next test covers)
     cfg = field_cfg(n_levels=8, log2_T=8)
     flat = S.init_params(cfg, 4).astype(np.float32)
+    live = reachable_params(cfg)
+    assert not live.all()
     field = lib.Field(cfg, params=flat)
     rng = np.random.default_rng(0)
     st = oracle.AdamState.zeros(flat.size)
     p_ref = flat.astype(np.float64)
     for k in range(3):
         g = (rng.normal(size=flat.size) * rng.choice([0, 1e-6, 1e-2, 1], size=flat.size)).astype(np.float32)
+        g[~live] = 0.0
         field.grads[: flat.size].copy_(_t(g))
         lib.optimizer_step(field)
         p_ref, st, _ = oracle.adam_step(p_ref, g.astype(np.float64), st, cfg)
         np.testing.assert_allclose(_np(field.flat_params()), p_ref, rtol=2e-6, atol=2e-8)
         assert float(field.grads.abs().max()) == 0.0
+
+
+def test_adam_leaves_unreachable_table_entries(lib):
+    # Adam visits only the reachable parameters: entries past a dense level's
+    # (N_l + 1)^3 vertices keep their values, gradients and moments (a step never
+    # gives them a gradient, so for the method this is the dense update exactly)
+    cfg = field_cfg(n_levels=8, log2_T=10)
+    flat = S.init_params(cfg, 6).astype(np.float32)
+    live = reachable_params(cfg)
+    dead = ~live
+    assert dead.sum() > 100
+    field = lib.Field(cfg, params=flat)
+    rng = np.random.default_rng(3)
+    g = rng.normal(size=flat.size).astype(np.float32)
+    field.grads[: flat.size].copy_(_t(g))
+    lib.optimizer_step(field)
+    st = oracle.AdamState.zeros(flat.size)
+    p_ref, st, _ = oracle.adam_step(flat.astype(np.float64), np.where(live, g, 0.0), st, cfg)
+    p = _np(field.flat_params())
+    np.testing.assert_allclose(p[live], p_ref[live], rtol=2e-6, atol=2e-8)
+    np.testing.assert_array_equal(p[dead], flat[dead])
+    np.testing.assert_array_equal(_np(field.grads[: flat.size])[dead], g[dead])
+    assert float(field.grads[: flat.size][_t(live)].abs().max()) == 0.0
+    assert float(field.adam_m[: flat.size][_t(dead)].abs().max()) == 0.0
 
 
 def test_training_curve_tracks_oracle(lib):
