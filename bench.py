@@ -1140,7 +1140,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                    "l2": "working set larger than L2: each step's Adam streams "
                          f"{4 * 4 * S.param_layout(f)['_total'][1] / 1e6:.0f} MB of parameter state",
                    "parallelism": f"replicas x{world}"},
-        "clocks": clocks, "e2e": e2e, "gpu_launches": (4 if fused else 5) * K, "roofline": roofline, "cpu_baseline": cpu,
+        "clocks": clocks, "e2e": e2e, "gpu_launches": (3 if fused else 5) * K, "roofline": roofline, "cpu_baseline": cpu,
         "mixed": mixed, "l2_roofline": l2, "psnr": psnr, "large": large, "mci": mci,
         "final_loss": losses[-1] if losses else None,
     }

@@ -3,7 +3,9 @@
 // scaling and the non-finite step skip.
 //
 //  k_adam_prep  one thread: reads the step's flags, decides skip / apply, updates
-//               the loss scale and step count, computes the bias corrections.
+//               the loss scale and step count, computes the bias corrections
+//               (adam_prologue; a training step whose loss kernel already ran it
+//               launches k_adam alone).
 //  k_adam       grid-stride float4 pass over the live ranges of the vector: m, v,
 //               p updated in place (torch.optim.Adam semantics: bias-corrected,
 //               eps outside the square root), grads zeroed, low-precision table
@@ -20,37 +22,14 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include "nh_adam_prep.cuh"
 #include "nh_internal.h"
 
 namespace nh {
 
-__global__ void k_adam_prep(DeviceState* st, float lr, float beta1, float beta2, int growth) {
+__global__ void k_adam_prep(DeviceState* st, AdamHyper h) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const uint32_t flags = st->flags;
-    const bool skip = (flags & NH_FLAG_NONFINITE) != 0u;
-    st->flags = 0u;
-    st->inv_scale = 1.f / st->loss_scale;
-    if (skip) {
-        st->skip = 1u;
-        st->last_flags = flags | NH_FLAG_SKIPPED;
-        if (growth > 0) {
-            st->loss_scale = fmaxf(st->loss_scale * 0.5f, 1.f);
-            st->good_steps = 0;
-        }
-        return;
-    }
-    st->skip = 0u;
-    st->last_flags = flags;
-    const int t = st->step + 1;
-    st->step = t;
-    st->step_size = lr / (1.f - powf(beta1, (float)t));
-    st->inv_bc2_sqrt = 1.f / sqrtf(1.f - powf(beta2, (float)t));
-    if (growth > 0) {
-        if (++st->good_steps >= growth) {
-            st->loss_scale = st->loss_scale * 2.f;
-            st->good_steps = 0;
-        }
-    }
+    adam_prologue(st, h);
 }
 
 template <typename LP>
@@ -210,10 +189,12 @@ static int sm_count() {
 
 cudaError_t launch_adam(const FieldArgs& fa, float* params, float* grads, float* m, float* v, int64_t n,
                         float lr, float beta1, float beta2, float eps, int growth_interval,
-                        cudaStream_t st) {
-    k_adam_prep<<<1, 32, 0, st>>>(fa.state, lr, beta1, beta2, growth_interval);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+                        cudaStream_t st, bool prologue) {
+    if (prologue) {
+        k_adam_prep<<<1, 32, 0, st>>>(fa.state, AdamHyper{lr, beta1, beta2, growth_interval});
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     // live ranges: each level's reachable entries (rounded up to whole float4s),
     // then the dense block; touching ranges are merged
     AdamRanges rg{};

@@ -14,6 +14,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "nh_eval.h"
+#include "nh_adam_prep.cuh"
 #include "nh_internal.h"
 #include "nh_mask.h"
 
@@ -463,15 +464,18 @@ static nh_status check_batch(const nh_field* f, const nh_geometry* g, const nh_r
     return NH_OK;
 }
 
-// Forward, loss and backward of one batch, accumulating into grads (R > 0).
+// Forward, loss and backward of one batch, accumulating into grads (R > 0). With
+// hyper (an optimizer step follows) the fused path's loss kernel also runs Adam's
+// prologue, and *prologue_done is set so that the optimizer launches k_adam alone.
 static nh_status run_accumulate(nh_field* f, const nh_geometry* g, int view, int R, const int32_t* pix,
                                 const float* a_meas, int N, uint64_t jitter, float* loss_dev, const RayWs& w,
-                                cudaStream_t st) {
+                                cudaStream_t st, const AdamHyper* hyper = nullptr, bool* prologue_done = nullptr) {
     const ViewArgs va = view_args(g, view, jitter);
     const int C = (N + 31) / 32;
     if (C <= kMaxFusedChunks) {   // whole rays fit a CTA: one fused forward + loss + backward kernel
-        NH_CUDA(launch_ray_train(f->fa, va, pix, a_meas, R, N, f->desc.loss, w.loss_part, loss_dev, st),
+        NH_CUDA(launch_ray_train(f->fa, va, pix, a_meas, R, N, f->desc.loss, w.loss_part, loss_dev, hyper, st),
                 "train_step fused");
+        if (prologue_done) *prologue_done = hyper != nullptr;
     } else {
         NH_CUDA(launch_ray_forward(f->fa, va, pix, R, N, w.ray_part, st), "train_step forward");
         NH_CUDA(launch_ray_loss(w.ray_part, R, C, a_meas, f->desc.loss, w.a_pred, w.dLdA, loss_dev, f->fa.state,
@@ -488,11 +492,14 @@ static nh_status run_train(nh_field* f, const nh_geometry* g, int view, int R, c
         if (loss_dev) NH_CUDA(cudaMemsetAsync(loss_dev, 0, sizeof(float), st), "train_step");
         return NH_OK;
     }
-    const nh_status s = run_accumulate(f, g, view, R, pix, a_meas, N, jitter, loss_dev, w, st);
+    const AdamHyper hyper{f->desc.lr, f->desc.beta1, f->desc.beta2, f->desc.growth_interval};
+    bool prologue_done = false;
+    const nh_status s = run_accumulate(f, g, view, R, pix, a_meas, N, jitter, loss_dev, w, st, &hyper,
+                                       &prologue_done);
     if (s != NH_OK) return s;
     NH_CUDA(launch_adam(f->fa, f->buf.params, f->buf.grads, f->buf.adam_m, f->buf.adam_v,
                         (int64_t)align_up(f->sizes.n_params, 4), f->desc.lr, f->desc.beta1, f->desc.beta2,
-                        f->desc.adam_eps, f->desc.growth_interval, st), "train_step adam");
+                        f->desc.adam_eps, f->desc.growth_interval, st, !prologue_done), "train_step adam");
     return NH_OK;
 }
 

@@ -36,16 +36,17 @@ extern template cudaError_t launch_query_volume_tt<float>(const FieldArgs&, int,
 extern template cudaError_t launch_query_volume_tt<__nv_bfloat16>(const FieldArgs&, int, float*, cudaStream_t);
 extern template cudaError_t launch_query_volume_tt<__half>(const FieldArgs&, int, float*, cudaStream_t);
 
-extern template cudaError_t launch_ray_train_tt<float>(const FieldArgs&, const ViewArgs&, const int32_t*, const float*, int, int, int, float*, float*, cudaStream_t);
-extern template cudaError_t launch_ray_train_tt<__nv_bfloat16>(const FieldArgs&, const ViewArgs&, const int32_t*, const float*, int, int, int, float*, float*, cudaStream_t);
-extern template cudaError_t launch_ray_train_tt<__half>(const FieldArgs&, const ViewArgs&, const int32_t*, const float*, int, int, int, float*, float*, cudaStream_t);
+extern template cudaError_t launch_ray_train_tt<float>(const FieldArgs&, const ViewArgs&, const int32_t*, const float*, int, int, int, float*, float*, const AdamHyper*, cudaStream_t);
+extern template cudaError_t launch_ray_train_tt<__nv_bfloat16>(const FieldArgs&, const ViewArgs&, const int32_t*, const float*, int, int, int, float*, float*, const AdamHyper*, cudaStream_t);
+extern template cudaError_t launch_ray_train_tt<__half>(const FieldArgs&, const ViewArgs&, const int32_t*, const float*, int, int, int, float*, float*, const AdamHyper*, cudaStream_t);
 
 cudaError_t launch_ray_train(const FieldArgs& fa, const ViewArgs& va, const int32_t* pix, const float* a_meas,
-                             int R, int N, int loss_kind, float* loss_part, float* loss_out, cudaStream_t st) {
+                             int R, int N, int loss_kind, float* loss_part, float* loss_out,
+                             const AdamHyper* hyper, cudaStream_t st) {
     switch (fa.precision) {
-        case NH_PREC_F32: return launch_ray_train_tt<float>(fa, va, pix, a_meas, R, N, loss_kind, loss_part, loss_out, st);
-        case NH_PREC_BF16: return launch_ray_train_tt<__nv_bfloat16>(fa, va, pix, a_meas, R, N, loss_kind, loss_part, loss_out, st);
-        case NH_PREC_F16: return launch_ray_train_tt<__half>(fa, va, pix, a_meas, R, N, loss_kind, loss_part, loss_out, st);
+        case NH_PREC_F32: return launch_ray_train_tt<float>(fa, va, pix, a_meas, R, N, loss_kind, loss_part, loss_out, hyper, st);
+        case NH_PREC_BF16: return launch_ray_train_tt<__nv_bfloat16>(fa, va, pix, a_meas, R, N, loss_kind, loss_part, loss_out, hyper, st);
+        case NH_PREC_F16: return launch_ray_train_tt<__half>(fa, va, pix, a_meas, R, N, loss_kind, loss_part, loss_out, hyper, st);
         default: return cudaErrorInvalidValue;
     }
 }

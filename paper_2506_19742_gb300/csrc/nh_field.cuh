@@ -18,6 +18,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "nh_adam_prep.cuh"
 #include "nh_device.cuh"
 #include "nh_internal.h"
 #include "nh_tmem.cuh"
@@ -871,14 +872,17 @@ __device__ __forceinline__ float ordered_partial_sum(const float* __restrict__ p
     return warp_sum(s);
 }
 
-// loss = (ordered sum of the CTA partials) / R.
+// loss = (ordered sum of the CTA partials) / R. With prologue set (an optimizer
+// step follows) the same thread then runs Adam's prologue, after the loss's own
+// non-finite check, so the step's launch count drops by one.
 static __global__ void k_train_loss(const float* __restrict__ part, int n_part, int R, float* loss_out,
-                                    DeviceState* state) {
+                                    DeviceState* state, AdamHyper hyper, int prologue) {
     const float s = ordered_partial_sum(part, n_part, threadIdx.x);
     if (threadIdx.x != 0) return;
     const float loss = s / (float)R;
     if (loss_out) *loss_out = loss;
     if (!isfinite(loss)) atomicOr(&state->flags, NH_FLAG_NONFINITE);
+    if (prologue) adam_prologue(state, hyper);
 }
 
 // ============================================================================ points
@@ -1222,7 +1226,8 @@ cudaError_t launch_query_volume_tt(const FieldArgs& fa, int D, float* out, cudaS
 // loss_part: >= kTrainParts floats of workspace.
 template <typename TT>
 cudaError_t launch_ray_train_tt(const FieldArgs& fa, const ViewArgs& va, const int32_t* pix, const float* a_meas,
-                                int R, int N, int loss_kind, float* loss_part, float* loss_out, cudaStream_t st) {
+                                int R, int N, int loss_kind, float* loss_part, float* loss_out,
+                                const AdamHyper* hyper, cudaStream_t st) {
     const int C = (N + 31) / 32;
     if (C > kMaxFusedChunks || R <= 0) return cudaErrorNotSupported;
     const int rpr = C <= kBwdWarps ? kBwdWarps / C : 1;
@@ -1241,7 +1246,8 @@ cudaError_t launch_ray_train_tt(const FieldArgs& fa, const ViewArgs& va, const i
         k<<<(unsigned)blocks, threads, sm, st>>>(fa, va, pix, a_meas, R, N, C, rpr, loss_kind, loss_part, tcols);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        k_train_loss<<<1, 32, 0, st>>>(loss_part, (int)blocks, R, loss_out, fa.state);
+        k_train_loss<<<1, 32, 0, st>>>(loss_part, (int)blocks, R, loss_out, fa.state,
+                                       hyper ? *hyper : AdamHyper{0.f, 0.f, 0.f, 0}, hyper ? 1 : 0);
     });
     return cudaGetLastError();
 }
@@ -1251,7 +1257,7 @@ cudaError_t launch_ray_train_tt(const FieldArgs& fa, const ViewArgs& va, const i
 // parallel.
 #define NH_INSTANTIATE_TRAIN(TT)                                                                            \
     template cudaError_t launch_ray_train_tt<TT>(const FieldArgs&, const ViewArgs&, const int32_t*, const float*, \
-                                                 int, int, int, float*, float*, cudaStream_t);
+                                                 int, int, int, float*, float*, const AdamHyper*, cudaStream_t);
 
 #define NH_INSTANTIATE_FIELD(TT)                                                                            \
     template cudaError_t launch_ray_forward_tt<TT>(const FieldArgs&, const ViewArgs&, const int32_t*, int, int, \

@@ -68,8 +68,12 @@ cudaError_t launch_ray_backward(const FieldArgs& fa, const ViewArgs& va, const i
 // samples); cudaErrorNotSupported for longer rays. loss_part: >= kTrainParts floats.
 constexpr int kTrainParts = 4096;
 constexpr int kMaxFusedChunks = 16;   // rays of up to 16 x 32 samples take the fused kernel
+// hyper != null: the loss kernel also runs the optimizer's prologue (an Adam step
+// follows, launched by launch_adam with prologue false).
+struct AdamHyper;
 cudaError_t launch_ray_train(const FieldArgs& fa, const ViewArgs& va, const int32_t* pix, const float* a_meas,
-                             int R, int N, int loss_kind, float* loss_part, float* loss_out, cudaStream_t st);
+                             int R, int N, int loss_kind, float* loss_part, float* loss_out,
+                             const AdamHyper* hyper, cudaStream_t st);
 // query (mu_gt == null) or MCI fit step (loss written to loss_out, CTA partials in loss_part)
 cudaError_t launch_points(const FieldArgs& fa, int n, const float* xyz, const float* mu_gt,
                           float* mu_out, float* loss_part, int n_part, float* loss_out,
@@ -77,7 +81,7 @@ cudaError_t launch_points(const FieldArgs& fa, int n, const float* xyz, const fl
 int         points_partials(int n);
 cudaError_t launch_adam(const FieldArgs& fa, float* params, float* grads, float* m, float* v,
                         int64_t n, float lr, float beta1, float beta2, float eps,
-                        int growth_interval, cudaStream_t st);
+                        int growth_interval, cudaStream_t st, bool prologue = true);
 cudaError_t launch_refresh_lowp(const float* params, void* lp, int64_t n, int precision,
                                 cudaStream_t st);
 cudaError_t launch_init_state(DeviceState* s, float loss_scale, cudaStream_t st);
