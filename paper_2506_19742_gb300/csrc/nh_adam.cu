@@ -97,8 +97,14 @@ __device__ __forceinline__ int64_t live_float4(const AdamRanges& rg, int64_t q, 
 // instruction is coalesced) and issues all of their loads before the first use,
 // so one resident wave keeps enough bytes in flight to stream at HBM speed.
 // Moments and zeroed gradients are written evict-first: only the next optimizer
-// pass reads them, while the parameters stay cacheable for the next gather.
+// pass reads them. The parameters the next gather reads stay cacheable: the
+// float32 vector on the FP32 path; on the 16-bit paths the low-precision copy,
+// while the float32 master copy, read only by the optimizer, streams
+// evict-first so that it does not displace the copy from L2.
 constexpr int kU = 4;
+// 16-bit paths: the float32 vector is a master copy that no gather reads.
+template <typename LP> constexpr bool kMasterOnly = true;
+template <> constexpr bool kMasterOnly<float> = false;
 
 template <typename LP>
 __global__ void __launch_bounds__(256, 3) k_adam(float* __restrict__ p, float* __restrict__ g,
@@ -129,7 +135,7 @@ __global__ void __launch_bounds__(256, 3) k_adam(float* __restrict__ p, float* _
                 const int64_t q = live_float4(rg, c, r);
                 qq[u] = q;
                 gg[u] = __ldcs(g4 + q);
-                pp[u] = p4[q];
+                pp[u] = kMasterOnly<LP> ? __ldcs(p4 + q) : p4[q];
                 mm[u] = __ldcs(m4 + q);
                 vv[u] = __ldcs(v4 + q);
             }
@@ -142,7 +148,10 @@ __global__ void __launch_bounds__(256, 3) k_adam(float* __restrict__ p, float* _
                 adam1(pp[u].y, mm[u].y, vv[u].y, gg[u].y * inv_scale, b1, b2, eps, step_size, ib2);
                 adam1(pp[u].z, mm[u].z, vv[u].z, gg[u].z * inv_scale, b1, b2, eps, step_size, ib2);
                 adam1(pp[u].w, mm[u].w, vv[u].w, gg[u].w * inv_scale, b1, b2, eps, step_size, ib2);
-                p4[q] = pp[u];
+                if constexpr (kMasterOnly<LP>)
+                    __stcs(p4 + q, pp[u]);
+                else
+                    p4[q] = pp[u];
                 __stcs(m4 + q, mm[u]);
                 __stcs(v4 + q, vv[u]);
                 __stcs(g4 + q, z4);
