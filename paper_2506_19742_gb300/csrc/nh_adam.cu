@@ -6,10 +6,13 @@
 //               the loss scale and step count, computes the bias corrections
 //               (adam_prologue; a training step whose loss kernel already ran it
 //               launches k_adam alone).
-//  k_adam       grid-stride float4 pass over the live ranges of the vector: m, v,
-//               p updated in place (torch.optim.Adam semantics: bias-corrected,
-//               eps outside the square root), grads zeroed, low-precision table
-//               copy refreshed. A skipped step only zeroes the grads.
+//  k_adam       float4 pass over the live ranges of the vector: m, v, p updated
+//               in place (torch.optim.Adam semantics: bias-corrected, eps outside
+//               the square root), grads zeroed, low-precision table copy
+//               refreshed. A skipped step only zeroes the grads. Each range gets
+//               its own share of the blocks, in proportion to its length, and
+//               those blocks sweep it grid-stride, so the inner loop indexes one
+//               contiguous range.
 //
 // Live ranges: a dense level l ((N_l + 1)^3 <= T) indexes only the first
 // (N_l + 1)^3 of its T entries, since a corner's index there is at most
@@ -78,24 +81,21 @@ __device__ __forceinline__ float adam1(float& p, float& m, float& v, float g, fl
 }
 
 // Float4 ranges of the flat vector that the pass visits, in order; range r starts
-// at float4 start4[r] and cum4[r] float4s precede it in the visit order.
+// at float4 start4[r], has cum4[r + 1] - cum4[r] float4s and is swept by blocks
+// block0[r] .. block0[r + 1] - 1.
 struct AdamRanges {
     int n;
     int64_t start4[kMaxLevels + 1];
     int64_t cum4[kMaxLevels + 2];
+    int block0[kMaxLevels + 2];
 };
 
-// Float4 index of the q-th visited group. q only grows along a thread's sweep, so
-// the range cursor r only moves forward.
-__device__ __forceinline__ int64_t live_float4(const AdamRanges& rg, int64_t q, int& r) {
-    while (r + 1 < rg.n && q >= rg.cum4[r + 1]) r++;
-    return rg.start4[r] + (q - rg.cum4[r]);
-}
-
 // n_lp (a multiple of 4) leading entries of the vector refresh lp.
-// Each thread owns kU float4 groups per sweep (strided by the grid so every
-// instruction is coalesced) and issues all of their loads before the first use,
-// so one resident wave keeps enough bytes in flight to stream at HBM speed.
+// Each thread owns kU float4 groups per sweep (strided by its range's blocks so
+// every instruction is coalesced) and issues all of their loads before the first
+// use, so one resident wave keeps enough bytes in flight to stream at HBM speed
+// (120 registers, two blocks per SM; held to three blocks per SM the kernel
+// spills and streams slower).
 // Moments and zeroed gradients are written evict-first: only the next optimizer
 // pass reads them. The parameters the next gather reads stay cacheable: the
 // float32 vector on the FP32 path; on the 16-bit paths the low-precision copy,
@@ -107,33 +107,40 @@ template <typename LP> constexpr bool kMasterOnly = true;
 template <> constexpr bool kMasterOnly<float> = false;
 
 template <typename LP>
-__global__ void __launch_bounds__(256, 3) k_adam(float* __restrict__ p, float* __restrict__ g,
+__global__ void __launch_bounds__(256) k_adam(float* __restrict__ p, float* __restrict__ g,
                                               float* __restrict__ m, float* __restrict__ v,
                                               const AdamRanges rg, LP* __restrict__ lp, int64_t n_lp,
                                               const DeviceState* st, float b1, float b2, float eps) {
-    const int64_t n4 = rg.cum4[rg.n];
-    const int64_t T = (int64_t)gridDim.x * blockDim.x;
-    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    float4* g4 = reinterpret_cast<float4*>(g);
+    // this block's range, read with constant indices (no local copy of the table)
+    int64_t n4 = 0, off = 0;
+    int bb = 0, be = 1;
+#pragma unroll
+    for (int k = 0; k < kMaxLevels + 1; k++) {
+        if (k < rg.n && (int)blockIdx.x >= rg.block0[k] && (int)blockIdx.x < rg.block0[k + 1]) {
+            n4 = rg.cum4[k + 1] - rg.cum4[k];
+            off = rg.start4[k];
+            bb = rg.block0[k];
+            be = rg.block0[k + 1];
+        }
+    }
+    const int64_t T = (int64_t)(be - bb) * blockDim.x;
+    const int64_t t0 = (int64_t)(blockIdx.x - bb) * blockDim.x + threadIdx.x;
+    float4* g4 = reinterpret_cast<float4*>(g) + off;
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    int r = 0;
     if (st->skip != 0u) {   // skipped step: only the gradients are cleared
-        for (int64_t q = t0; q < n4; q += T) __stcs(g4 + live_float4(rg, q, r), z4);
+        for (int64_t q = t0; q < n4; q += T) __stcs(g4 + q, z4);
         return;
     }
     const float inv_scale = st->inv_scale, step_size = st->step_size, ib2 = st->inv_bc2_sqrt;
-    float4* p4 = reinterpret_cast<float4*>(p);
-    float4* m4 = reinterpret_cast<float4*>(m);
-    float4* v4 = reinterpret_cast<float4*>(v);
+    float4* p4 = reinterpret_cast<float4*>(p) + off;
+    float4* m4 = reinterpret_cast<float4*>(m) + off;
+    float4* v4 = reinterpret_cast<float4*>(v) + off;
     for (int64_t base = t0; base < n4; base += T * kU) {
         float4 gg[kU], pp[kU], mm[kU], vv[kU];
-        int64_t qq[kU];
 #pragma unroll
         for (int u = 0; u < kU; u++) {
-            const int64_t c = base + u * T;
-            if (c < n4) {
-                const int64_t q = live_float4(rg, c, r);
-                qq[u] = q;
+            const int64_t q = base + u * T;
+            if (q < n4) {
                 gg[u] = __ldcs(g4 + q);
                 pp[u] = kMasterOnly<LP> ? __ldcs(p4 + q) : p4[q];
                 mm[u] = __ldcs(m4 + q);
@@ -142,8 +149,8 @@ __global__ void __launch_bounds__(256, 3) k_adam(float* __restrict__ p, float* _
         }
 #pragma unroll
         for (int u = 0; u < kU; u++) {
-            if (base + u * T < n4) {
-                const int64_t q = qq[u];
+            const int64_t q = base + u * T;
+            if (q < n4) {
                 adam1(pp[u].x, mm[u].x, vv[u].x, gg[u].x * inv_scale, b1, b2, eps, step_size, ib2);
                 adam1(pp[u].y, mm[u].y, vv[u].y, gg[u].y * inv_scale, b1, b2, eps, step_size, ib2);
                 adam1(pp[u].z, mm[u].z, vv[u].z, gg[u].z * inv_scale, b1, b2, eps, step_size, ib2);
@@ -155,7 +162,7 @@ __global__ void __launch_bounds__(256, 3) k_adam(float* __restrict__ p, float* _
                 __stcs(m4 + q, mm[u]);
                 __stcs(v4 + q, vv[u]);
                 __stcs(g4 + q, z4);
-                if ((q << 2) < n_lp) store_lp<LP>(lp, q << 2, pp[u]);
+                if (((off + q) << 2) < n_lp) store_lp<LP>(lp, (off + q) << 2, pp[u]);
             }
         }
     }
@@ -239,6 +246,19 @@ cudaError_t launch_adam(const FieldArgs& fa, float* params, float* grads, float*
     const int64_t cap = (int64_t)sm_count() * (per_sm > 0 ? per_sm : 1);
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
+    // blocks per range in proportion to its float4s, at least one each
+    {
+        int b0 = 0;
+        for (int r = 0; r < rg.n; r++) {
+            const int64_t len = rg.cum4[r + 1] - rg.cum4[r];
+            int64_t nb = (len * blocks + n4 - 1) / n4;
+            if (nb < 1) nb = 1;
+            rg.block0[r] = b0;
+            b0 += (int)nb;
+        }
+        rg.block0[rg.n] = b0;
+        blocks = b0;
+    }
     if (fa.precision == NH_PREC_BF16)
         k_adam<__nv_bfloat16><<<(unsigned)blocks, 256, 0, st>>>(params, grads, m, v, rg,
             (__nv_bfloat16*)fa.tables_lp, fa.n_table, fa.state, beta1, beta2, eps);
