@@ -472,9 +472,13 @@ static nh_status run_accumulate(nh_field* f, const nh_geometry* g, int view, int
                                 cudaStream_t st, const AdamHyper* hyper = nullptr, bool* prologue_done = nullptr) {
     const ViewArgs va = view_args(g, view, jitter);
     const int C = (N + 31) / 32;
-    if (C <= kMaxFusedChunks) {   // whole rays fit a CTA: one fused forward + loss + backward kernel
-        NH_CUDA(launch_ray_train(f->fa, va, pix, a_meas, R, N, f->desc.loss, w.loss_part, loss_dev, hyper, st),
-                "train_step fused");
+    // whole rays fit a CTA: one fused forward + loss + backward kernel; it declines
+    // (launching nothing) where a CTA's activations exceed tensor memory
+    const cudaError_t fe = C <= kMaxFusedChunks
+        ? launch_ray_train(f->fa, va, pix, a_meas, R, N, f->desc.loss, w.loss_part, loss_dev, hyper, st)
+        : cudaErrorNotSupported;
+    if (fe != cudaErrorNotSupported) {
+        NH_CUDA(fe, "train_step fused");
         if (prologue_done) *prologue_done = hyper != nullptr;
     } else {
         NH_CUDA(launch_ray_forward(f->fa, va, pix, R, N, w.ray_part, st), "train_step forward");

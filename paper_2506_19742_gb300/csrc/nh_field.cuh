@@ -268,6 +268,7 @@ static __global__ void __launch_bounds__(1024) k_ray_loss(const float* __restric
 constexpr int kStage = 32 * kW;
 __host__ __device__ constexpr int warp_scratch_floats() { return kStage + 32 * kW; }
 constexpr int kBwdWarps = 8;
+constexpr int kMidTrainWarps = 12;   // rays of 9..12 chunks: 168 registers a thread
 constexpr int kMaxTrainWarps = kMaxFusedChunks;
 
 __device__ __forceinline__ int swz(int s, int j) {   // column j of dz row s
@@ -641,15 +642,17 @@ __host__ __device__ inline int bwd_warp_floats(int precision) {
     return precision == NH_PREC_F32 ? warp_scratch_floats() : kMmaWarpFloats;
 }
 
-// FP32 training CTAs of at most this many warps split the MLP weights once at
-// staging (the lo tiles, H kW kW floats, still leave room for two CTAs per SM).
-constexpr int kPresplitMaxWarps = 6;
-
-static size_t bwd_smem_bytes(const FieldArgs& fa, int nwarps = kBwdWarps) {
+// FP32 fused training CTAs that split the MLP weights once at staging add the lo
+// tiles (H kW kW floats) to their shared memory: CTAs of at most six warps always
+// (two still fit per SM), CTAs of 9..12 warps (one per SM in any case) when the
+// total stays within the opt-in limit. Eight-warp CTAs would lose their second CTA
+// per SM to the 16 KB, and 16-warp CTAs, compiled for 128 registers, spill more
+// with the split operands, so both split on load.
+static size_t bwd_smem_bytes(const FieldArgs& fa, int nwarps = kBwdWarps, bool presplit = false) {
     const int ndp = (fa.n_dense + 3) & ~3;
     size_t b = (size_t)(2 * ndp + kMaxD + nwarps * bwd_warp_floats(fa.precision)) * sizeof(float);
     if (fa.precision != NH_PREC_F32) b += (size_t)fa.H * kMmaLayerElems * 2;
-    else if (nwarps <= kPresplitMaxWarps) b += (size_t)fa.H * kW * kW * sizeof(float);
+    else if (presplit) b += (size_t)fa.H * kW * kW * sizeof(float);
     if (512u / bwd_tmem_cols(fa, nwarps) < 2u && b < 120 * 1024) b = 120 * 1024;
     return b;
 }
@@ -778,10 +781,13 @@ struct TrainCarry<D, G, __half> {
 // NW: most warps a CTA launches with. CTAs of at most six warps (rays of three,
 // five or six chunks) are compiled with the register budget of two six-warp CTAs
 // per SM instead of two eight-warp ones; CTAs of 9..16 warps (one long ray each)
-// run one per SM. On the 16-bit path the six-warp CTAs (5 or 6 warps launched)
+// run one per SM, with the register budget of 12 warps (168 a thread) up to 12
+// warps and of 16 warps (128) above. On the 16-bit path the six-warp CTAs (5 or 6 warps launched)
 // take the CTA-cooperative MLP weight gradient; the larger CTAs, compiled for 128
 // registers, keep the per-warp shared atomics, which need fewer registers.
-template <int D, int G, typename TT, int NW>
+// PS (FP32 path only): the CTA splits the MLP weights once at staging; its shared
+// memory holds the lo tiles (bwd_smem_bytes with presplit).
+template <int D, int G, typename TT, int NW, bool PS>
 __global__ void __launch_bounds__(NW * 32, NW > 8 ? 1 : 2)
 k_ray_train(FieldArgs fa, ViewArgs va, const int32_t* __restrict__ pix, const float* __restrict__ a_meas, int R,
             int N, int C, int rpr, int loss_kind, float* __restrict__ loss_part, uint32_t tcols) {
@@ -791,7 +797,6 @@ k_ray_train(FieldArgs fa, ViewArgs va, const int32_t* __restrict__ pix, const fl
     __shared__ float s_g[kMaxTrainWarps];
     __shared__ float s_lr[kMaxTrainWarps];
     __shared__ float s_loss;
-    constexpr bool PS = NW <= kPresplitMaxWarps;
     const BwdCta cta = bwd_begin<TT, PS>(fa, smem, &s_tmem, tcols);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int rl = warp / C, c = warp - rl * C;
@@ -1219,10 +1224,11 @@ cudaError_t launch_query_volume_tt(const FieldArgs& fa, int D, float* out, cudaS
 }
 
 // Fused training step (k_ray_train) when a ray has at most kMaxFusedChunks chunks of
-// 32 samples; returns cudaErrorNotSupported otherwise (the caller then runs forward,
-// loss and backward as separate kernels). Rays of up to 8 chunks are packed
-// 8 / C to a CTA of C * (8 / C) warps, two CTAs per SM; longer rays take one CTA of C
-// warps each, one CTA per SM (its TMEM groups fill the SM's 512 columns).
+// 32 samples and the CTA's activations fit the SM's 512 TMEM columns; returns
+// cudaErrorNotSupported otherwise, before launching anything (the caller then runs
+// forward, loss and backward as separate kernels). Rays of up to 8 chunks are
+// packed 8 / C to a CTA of C * (8 / C) warps, two CTAs per SM; longer rays take one
+// CTA of C warps each, one CTA per SM (its TMEM groups fill the SM's 512 columns).
 // loss_part: >= kTrainParts floats of workspace.
 template <typename TT>
 cudaError_t launch_ray_train_tt(const FieldArgs& fa, const ViewArgs& va, const int32_t* pix, const float* a_meas,
@@ -1234,11 +1240,18 @@ cudaError_t launch_ray_train_tt(const FieldArgs& fa, const ViewArgs& va, const i
     const int nw = rpr * C;
     const int threads = nw * 32;
     const long long ngroups = ((long long)R + rpr - 1) / rpr;
-    const size_t sm = bwd_smem_bytes(fa, nw);
+    constexpr bool kF32 = !kMmaPath<TT>;
     const uint32_t tcols = bwd_tmem_cols(fa, nw);
+    if (tcols > 512u) return cudaErrorNotSupported;   // deep MLPs with long rays: split path
+    const bool ps = kF32 && (nw <= 6 || (nw > kBwdWarps && nw <= kMidTrainWarps &&
+                                         bwd_smem_bytes(fa, nw, true) + 1024 <= 227 * 1024));
+    const size_t sm = bwd_smem_bytes(fa, nw, ps);
     NH_DISPATCH_DG(fa, {
-        auto k = nw <= 6 ? k_ray_train<D_, G_, TT, 6>
-                         : (nw <= kBwdWarps ? k_ray_train<D_, G_, TT, kBwdWarps> : k_ray_train<D_, G_, TT, kMaxTrainWarps>);
+        auto k = nw <= 6 ? k_ray_train<D_, G_, TT, 6, kF32>
+                 : nw <= kBwdWarps ? k_ray_train<D_, G_, TT, kBwdWarps, false>
+                 : nw <= kMidTrainWarps
+                       ? (ps ? k_ray_train<D_, G_, TT, kMidTrainWarps, kF32> : k_ray_train<D_, G_, TT, kMidTrainWarps, false>)
+                       : k_ray_train<D_, G_, TT, kMaxTrainWarps, false>;
         cudaError_t e = set_smem(k, sm);
         if (e != cudaSuccess) return e;
         long long blocks = train_grid(k, sm, tcols, ngroups, threads);

@@ -78,6 +78,27 @@ def replace(cfg, **kw):
     return dataclasses.replace(cfg, **kw)
 
 
+def kink_free_rays(cache, n_rays, rel=4e-6):
+    """Indices of the batch's rays none of whose samples has a hidden ReLU unit
+    within float32 rounding of its kink (|z| <= rel * (sum_i |W_ji a_i| + |b_j|), the
+    criterion of table_kink_allowance). At such a unit either branch is a correct
+    float32 result; a batch without them has one correct gradient, which FP32
+    implementations must reach within rounding in every parameter group."""
+    p, fc, hit, delta, N = cache
+    keep = np.ones(n_rays, dtype=bool)
+    if fc is None:
+        return np.nonzero(keep)[0]
+    x, res, T, mask, ncache, mu, acts, zs = fc
+    Ws, bs = p["W"], p["b"]
+    amb = np.zeros(len(mu), dtype=bool)
+    for k in range(len(Ws) - 1):
+        scale = np.abs(acts[k]) @ np.abs(Ws[k]).T + np.abs(bs[k])
+        amb |= np.any(np.abs(zs[k]) <= rel * scale, axis=1)
+    hit_rays = np.nonzero(hit)[0]
+    keep[np.unique(hit_rays[np.nonzero(amb)[0] // N])] = False
+    return np.nonzero(keep)[0]
+
+
 def table_kink_allowance(cache, dLdA, cfg, rel=4e-6):
     """Elementwise bound on how far a float32 implementation's hash-table gradient
     may lie from the oracle's because a ReLU unit whose pre-activation is within

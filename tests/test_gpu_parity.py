@@ -14,6 +14,7 @@ import pytest
 import oracle
 import synthetic as S
 from _cases import (C4_SUB, C4_SUB_GEOM, C4_SUB_N, batch, c4_subinstance, field_cfg, fp32_gradient_errors,
+                    kink_free_rays,
                     hit_pixels, oracle_geom, replace, rounded_tables)
 
 pytestmark = pytest.mark.gpu
@@ -252,6 +253,38 @@ def test_train_step_fused_and_split_paths_match_oracle(lib, precision, N):
     flags, _, step = field.poll_status()
     assert step == 1 and flags == 0
     assert not np.array_equal(_np(field.flat_params()), flat)
+
+
+@pytest.mark.parametrize("hidden", [6, 8])
+def test_deep_mlp_with_long_rays_takes_the_split_kernels(lib, hidden):
+    """A fused CTA keeps 32 H tensor-memory columns a thread for every group of four
+    warps. With 6 or 8 hidden layers and rays of 10 chunks (N = 300) that exceeds the
+    SM's 512 columns, so accumulate_step declines the fused kernel before launching
+    anything and runs forward, loss and backward as separate kernels; the loss and
+    every gradient group still match the oracle (FP32 bounds). Rays with a sample
+    at a ReLU kink (within float32 rounding, where either branch is correct) are
+    left out of the batch, so that every group has one correct gradient; deep
+    random-init MLPs put a few such units in the first layers."""
+    N = 300
+    cfg = field_cfg(n_levels=16, hidden_layers=hidden, log2_T=12, max_res=256, loss_scale_init=1.0)
+    flat = S.init_params(cfg, 41, table_scale=0.5).astype(np.float32)
+    field = lib.Field(cfg, params=flat)
+    geom = lib.Geometry.from_config(GEOM)
+    og = oracle_geom(GEOM)
+    pix = batch(GEOM, 3, 120, seed=hidden, n_miss=2)
+    _, cache = oracle.render_forward(flat.astype(np.float64), cfg, og, 3, pix, N)
+    pix = pix[kink_free_rays(cache, len(pix))]
+    assert len(pix) >= 80
+    a_meas = np.random.default_rng(hidden).uniform(0, 0.8, size=len(pix)).astype(np.float32)
+    A, cache = oracle.render_forward(flat.astype(np.float64), cfg, og, 3, pix, N)
+    ref_loss, dLdA = oracle.loss_and_grad(A, a_meas, S.LOSS_MSE)
+    g_ref = oracle.render_backward(cache, dLdA, cfg)
+    ws = lib.workspace(lib.step_workspace_bytes(field, len(pix), N))
+    loss_t = torch.zeros(1, device="cuda")
+    lib.accumulate_step(field, geom, 3, _t(pix), _t(a_meas), N, loss_t, ws)
+    assert abs(_np(loss_t)[0] - ref_loss) <= 1e-5 * ref_loss
+    bad = fp32_gradient_errors(_np(field.flat_grads()), g_ref, cfg, cache, dLdA)
+    assert not bad, (f"H={hidden} N={N}", bad)
 
 
 @pytest.mark.parametrize("N", [192, 520])
