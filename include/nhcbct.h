@@ -230,7 +230,10 @@ nh_status train_step(nh_field* f, const nh_geometry* g, const nh_ray_batch* b, f
 /* train_step without the optimizer: forward, loss (written to loss_dev[0]) and
  * backward, ACCUMULATING into grads, so that several batches can be accumulated
  * before one optimizer_step. When every ray has at most 16 chunks of 32 samples
- * (n_samples <= 512) this is one fused kernel per call. */
+ * (n_samples <= 512) this is one fused kernel (plus the ordered loss sum) per
+ * call, unless a CTA's activations would exceed tensor memory (more than four
+ * hidden layers with rays of more than 8 chunks); then, as for longer rays, the
+ * forward, loss and backward run as separate kernels, with the same results. */
 nh_status accumulate_step(nh_field* f, const nh_geometry* g, const nh_ray_batch* b, float* loss_dev,
                           void* ws, size_t ws_bytes, void* stream);
 /* The same step from HOST arrays (pinned memory for asynchrony): pix_host and
