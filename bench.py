@@ -3,12 +3,16 @@
 
 A step is one pass of the whole hot path over one batch: ray setup and sampling,
 hash gather, Normalized Hash Encoder, MLP, Beer-Lambert ray sum, loss, the
-backward (MLP, LN, hash scatter) and Adam over every parameter. The default
+backward (MLP, LN, hash scatter) and Adam over every parameter a step can reach
+(a dense level's entries past its (N_l + 1)^3 grid vertices are never reached and
+Adam leaves them as they are). The default
 workload is the paper-scale FP32 configuration: a 128^3 textured ellipsoid
 phantom, 50 views of a 256x256 detector, L=16 F=2 T=2^19 levels 16..2048,
 LayerNorm, 4x32 MLP, 2048 rays x 192 samples per step. Inputs are synthetic
 (seeded phantom projected by the library, Poisson noise at I0 = 1e5); every
-batch uses pixels whose ray meets the volume.
+batch uses pixels whose ray meets the volume, in ascending pixel id. The e2e
+number copies each step's pixels and measurements from pinned host memory and
+its loss back, and reads every loss on the host one step behind.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
