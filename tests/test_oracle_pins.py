@@ -381,6 +381,49 @@ def test_adam_matches_torch_optim():
     assert skipped and st2.t == st.t and np.array_equal(p2, p)
 
 
+def test_adam_leaves_zero_gradient_zero_moment_entries_bit_for_bit():
+    # the step of an entry whose gradient and moments are zero is exactly zero:
+    # m = v = 0 give lr * 0 / (0 + eps), so p comes back with the same bits, at
+    # every step count (the bias corrections multiply zeros)
+    cfg = TINY_F
+    rng = np.random.default_rng(11)
+    p = rng.normal(size=64)
+    p0 = p.copy()
+    st = oracle.AdamState.zeros(64)
+    for step in range(5):
+        g = rng.normal(size=64)
+        g[:16] = 0.0
+        p, st, _ = oracle.adam_step(p, g, st, cfg)
+    assert np.array_equal(p[:16], p0[:16])
+    assert not np.any(st.m[:16]) and not np.any(st.v[:16])
+    assert not np.array_equal(p[16:], p0[16:])
+
+
+def test_dense_levels_give_no_gradient_past_their_grid_vertices():
+    # a dense level (N_l + 1)^3 <= T indexes corner (x, y, z) at x + y (N + 1) +
+    # z (N + 1)^2 <= (N + 1)^3 - 1, so the backward never reaches its later entries
+    # (the optimizer may skip them); the hashed levels' entries are all reachable
+    from _cases import batch, field_cfg, oracle_geom
+    from oracle.encoding import is_dense, level_resolutions
+    cfg = field_cfg(n_levels=8, log2_T=12, base_res=4, max_res=48)
+    geom = S.GeometryConfig(n_views=6, det_nu=40, det_nv=36)
+    flat = S.init_params(cfg, 3, table_scale=0.5).astype(np.float64)
+    pix = batch(geom, 2, 150, seed=1)
+    A, cache = oracle.render_forward(flat, cfg, oracle_geom(geom), 2, pix, 24)
+    _, dLdA = oracle.loss_and_grad(A, np.zeros(len(pix)), S.LOSS_MSE)
+    g = oracle.render_backward(cache, dLdA, cfg)
+    T, F = 2 ** cfg.log2_T, cfg.n_feat
+    dense = 0
+    for l, res in enumerate(level_resolutions(cfg.n_levels, cfg.base_res, cfg.max_res)):
+        lev = g[l * T * F:(l + 1) * T * F]
+        if is_dense(res, T):
+            dense += 1
+            n_l = (res + 1) ** 3
+            assert not np.any(lev[n_l * F:]), (l, res)
+            assert np.any(lev[:n_l * F])
+    assert dense >= 3
+
+
 # ---------------------------------------------------------------- projector
 def _ellipsoid_chord(o, d, E):
     """Exact line integral of a top-index-wins ellipsoid phantom along o + t d (t >= 0),
