@@ -1142,7 +1142,10 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                    "volume": w.vol_D, "views": w.geometry.n_views,
                    "detector": [w.geometry.det_nu, w.geometry.det_nv],
                    "l2": "working set larger than L2: each step's Adam streams "
-                         f"{4 * 4 * S.param_layout(f)['_total'][1] / 1e6:.0f} MB of parameter state",
+                         f"{4 * 4 * optimizer_params(f) / 1e6:.0f} MB of parameter state",
+                   "optimizer": f"Adam (torch semantics), dense over the {optimizer_params(f)} parameters a step "
+                                f"can reach of {S.param_layout(f)['_total'][1]}; the others (dense levels' entries "
+                                "past their (N+1)^3 vertices) never get a gradient, and their update is exactly zero",
                    "parallelism": f"replicas x{world}"},
         "clocks": clocks, "e2e": e2e, "gpu_launches": (3 if fused else 5) * K, "roofline": roofline, "cpu_baseline": cpu,
         "mixed": mixed, "l2_roofline": l2, "psnr": psnr, "large": large, "mci": mci,
