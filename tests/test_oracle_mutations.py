@@ -27,6 +27,9 @@ MUTATIONS = [
     ("hash primes transposed (Sec. 2.1, spatial hash)", "encoding.py",
      "np.uint32(2654435761), np.uint32(805459861)",
      "np.uint32(805459861), np.uint32(2654435761)"),
+    ("dense-level index stride N + 2 instead of N + 1 (Sec. 2.1, multiresolution grid)", "encoding.py",
+     "s = np.uint32(n + 1)",
+     "s = np.uint32(n + 2)"),
     ("trilinear corner weight swapped (Sec. 2.1)", "encoding.py",
      "(w64[:, k] if b[k] else (1.0 - w64[:, k]))",
      "((1.0 - w64[:, k]) if b[k] else w64[:, k])"),
